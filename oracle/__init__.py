@@ -1,0 +1,272 @@
+"""FP64 CPU oracle of the D3Q27 central-moment LBM with forcing -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import
+this package.  The product library (``paper_1905_10182_gb300``) never imports, links or runs
+anything here, and this package imports nothing from it.
+
+The arithmetic lives in ``cmlbm_oracle.c`` (plain C, FP64, OpenMP over nodes); this module
+builds it with gcc and exposes numpy-friendly wrappers.  Populations are full values f_i
+(not deviations) in the layout f[i, z, y, x].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "cmlbm_oracle.c")
+LIB = os.path.join(HERE, "_build", "libcmlbm_oracle.so")
+
+Q = 27
+COLL_LITERAL, COLL_PAPER, COLL_BGK, COLL_NONE = 0, 1, 2, 3
+FORCE_NONE, FORCE_UNIFORM, FORCE_KOLMOGOROV, FORCE_FIELD, FORCE_SHAN_CHEN = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (portable flags only: x86_64 and aarch64)."""
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    srcs = [SRC, os.path.join(HERE, "cmlbm_oracle.h")]
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(s) for s in srcs)):
+        return LIB
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-o", tmp, SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("omega", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("walls_y", ctypes.c_int),
+        ("mask", ctypes.c_void_p),
+        ("collision", ctypes.c_int),
+        ("eq_order", ctypes.c_int), ("force_order", ctypes.c_int),
+        ("lambda_", ctypes.c_void_p),
+        ("force_kind", ctypes.c_int),
+        ("force", ctypes.c_double * 3),
+        ("G", ctypes.c_double),
+        ("fx", ctypes.c_void_p), ("fy", ctypes.c_void_p), ("fz", ctypes.c_void_p),
+        ("threads", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.orc_velocities.argtypes = [ctypes.POINTER(ctypes.c_int)]
+        L.orc_weights.argtypes = [dp]
+        L.orc_opposite.argtypes = [ctypes.c_int]
+        L.orc_opposite.restype = ctypes.c_int
+        L.orc_hermite.argtypes = [ctypes.c_int] * 4
+        L.orc_hermite.restype = ctypes.c_double
+        L.orc_equilibrium.argtypes = [ctypes.c_double, dp, ctypes.c_int, dp]
+        L.orc_forcing_term.argtypes = [dp, dp, ctypes.c_int, dp]
+        L.orc_basis.argtypes = [dp, dp]
+        L.orc_central_moments.argtypes = [dp, dp, dp]
+        L.orc_inverse_literal.argtypes = [dp, dp, dp]
+        L.orc_inverse_literal.restype = ctypes.c_int
+        L.orc_inverse_fast.argtypes = [dp, dp, dp]
+        for name in ("orc_collide",):
+            getattr(L, name).argtypes = [ctypes.POINTER(_Desc), dp, dp, dp]
+            getattr(L, name).restype = ctypes.c_int
+        L.orc_force_field.argtypes = [ctypes.POINTER(_Desc), dp, dp]
+        L.orc_force_field.restype = ctypes.c_int
+        L.orc_macroscopic.argtypes = [ctypes.POINTER(_Desc), dp, dp, dp]
+        L.orc_macroscopic.restype = ctypes.c_int
+        L.orc_init_equilibrium.argtypes = [ctypes.POINTER(_Desc), dp, dp, dp]
+        L.orc_init_equilibrium.restype = ctypes.c_int
+        L.orc_step.argtypes = [ctypes.POINTER(_Desc), dp, ctypes.c_int]
+        L.orc_step.restype = ctypes.c_int
+        L.orc_step_sampled.argtypes = [ctypes.POINTER(_Desc), dp, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.c_int, dp]
+        L.orc_step_sampled.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _vec(v, n=3):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(n))
+    return a
+
+
+# --------------------------------------------------------------------------- lattice
+def velocities() -> np.ndarray:
+    c = (ctypes.c_int * (Q * 3))()
+    lib().orc_velocities(c)
+    return np.array(c[:], dtype=np.int64).reshape(Q, 3)
+
+
+def weights() -> np.ndarray:
+    w = np.zeros(Q)
+    lib().orc_weights(_dp(w))
+    return w
+
+
+def opposite(i: int) -> int:
+    return lib().orc_opposite(i)
+
+
+def hermite(i: int, nx: int, ny: int, nz: int) -> float:
+    return lib().orc_hermite(i, nx, ny, nz)
+
+
+def equilibrium(rho, u, order=6) -> np.ndarray:
+    out = np.zeros(Q)
+    uu = _vec(u)
+    lib().orc_equilibrium(float(rho), _dp(uu), int(order), _dp(out))
+    return out
+
+
+def forcing_term(F, u, order=6) -> np.ndarray:
+    out = np.zeros(Q)
+    FF, uu = _vec(F), _vec(u)
+    lib().orc_forcing_term(_dp(FF), _dp(uu), int(order), _dp(out))
+    return out
+
+
+def basis(u) -> np.ndarray:
+    T = np.zeros((Q, Q))
+    uu = _vec(u)
+    lib().orc_basis(_dp(uu), _dp(T))
+    return T
+
+
+def central_moments(u, v) -> np.ndarray:
+    k = np.zeros(Q)
+    uu, vv = _vec(u), _vec(v, Q)
+    lib().orc_central_moments(_dp(uu), _dp(vv), _dp(k))
+    return k
+
+
+def inverse_literal(u, k) -> np.ndarray:
+    v = np.zeros(Q)
+    uu, kk = _vec(u), _vec(k, Q)
+    st = lib().orc_inverse_literal(_dp(uu), _dp(kk), _dp(v))
+    if st:
+        raise RuntimeError(f"orc_inverse_literal failed ({st})")
+    return v
+
+
+def inverse_fast(u, k) -> np.ndarray:
+    v = np.zeros(Q)
+    uu, kk = _vec(u), _vec(k, Q)
+    lib().orc_inverse_fast(_dp(uu), _dp(kk), _dp(v))
+    return v
+
+
+# --------------------------------------------------------------------------- grid
+class Grid:
+    """Parameters of an oracle run; owns the numpy arrays the C descriptor points at."""
+
+    def __init__(self, nx, ny, nz, nu=None, omega=None, rho0=1.0, walls_y=False, mask=None,
+                 collision=COLL_PAPER, eq_order=6, force_order=6, lambdas=None,
+                 force_kind=FORCE_NONE, force=(0.0, 0.0, 0.0), G=0.0, field=None, threads=0):
+        if omega is None:
+            omega = 1.0 / (3.0 * nu + 0.5)
+        self.shape = (int(nz), int(ny), int(nx))
+        self.N = int(nx) * int(ny) * int(nz)
+        d = _Desc()
+        d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
+        d.omega = float(omega)
+        d.rho0 = float(rho0)
+        d.walls_y = int(bool(walls_y))
+        self._mask = None
+        if mask is not None:
+            self._mask = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+            d.mask = self._mask.ctypes.data
+        d.collision = int(collision)
+        d.eq_order, d.force_order = int(eq_order), int(force_order)
+        self._lam = None
+        if lambdas is not None:
+            self._lam = _vec(lambdas, Q)
+            d.lambda_ = self._lam.ctypes.data
+        d.force_kind = int(force_kind)
+        for k in range(3):
+            d.force[k] = float(force[k])
+        d.G = float(G)
+        self._field = None
+        if field is not None:
+            self._field = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1)) for a in field]
+            d.fx, d.fy, d.fz = (a.ctypes.data for a in self._field)
+        d.threads = int(threads)
+        self.desc = d
+
+    def _check(self, st, what):
+        if st:
+            raise RuntimeError(f"oracle {what} failed with status {st}")
+
+    def collide(self, f, F=(0.0, 0.0, 0.0)) -> np.ndarray:
+        ff, FF = _vec(f, Q), _vec(F)
+        out = np.zeros(Q)
+        self._check(lib().orc_collide(ctypes.byref(self.desc), _dp(ff), _dp(FF), _dp(out)), "collide")
+        return out
+
+    def init_equilibrium(self, rho, u) -> np.ndarray:
+        rho = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, dtype=np.float64), self.shape)).reshape(-1)
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(3, -1))
+        f = np.zeros((Q,) + self.shape)
+        self._check(lib().orc_init_equilibrium(ctypes.byref(self.desc), _dp(rho), _dp(u), _dp(f)), "init")
+        return f
+
+    def step(self, f: np.ndarray, nsteps: int = 1) -> np.ndarray:
+        """Advance a copy of f (shape (27, nz, ny, nx)) by nsteps; returns the new array."""
+        g = np.ascontiguousarray(f, dtype=np.float64).copy()
+        self._check(lib().orc_step(ctypes.byref(self.desc), _dp(g), int(nsteps)), "step")
+        return g
+
+    def step_sampled(self, f: np.ndarray, nodes) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.int64))
+        out = np.zeros((len(nodes), Q))
+        self._check(lib().orc_step_sampled(ctypes.byref(self.desc), _dp(f),
+                                           nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                           len(nodes), _dp(out)), "step_sampled")
+        return out
+
+    def force_field(self, f) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        F = np.zeros((3,) + self.shape)
+        self._check(lib().orc_force_field(ctypes.byref(self.desc), _dp(f), _dp(F)), "force_field")
+        return F
+
+    def macroscopic(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        rho = np.zeros(self.shape)
+        u = np.zeros((3,) + self.shape)
+        self._check(lib().orc_macroscopic(ctypes.byref(self.desc), _dp(f), _dp(rho), _dp(u)), "macroscopic")
+        return rho, u
+
+
+# --------------------------------------------------------------------------- diagnostics
+def kinetic_energy(u, fluid=None) -> float:
+    """Mean of |u|^2 / 2 over fluid nodes (FP64)."""
+    e = 0.5 * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)
+    return float(e[fluid].mean() if fluid is not None else e.mean())
+
+
+def enstrophy(u) -> float:
+    """Mean of |curl u|^2 / 2 with second-order central differences on a periodic grid.
+    u has shape (3, nz, ny, nx)."""
+    def d(a, axis):
+        return 0.5 * (np.roll(a, -1, axis=axis) - np.roll(a, 1, axis=axis))
+    ux, uy, uz = u
+    wx = d(uz, 1) - d(uy, 0)
+    wy = d(ux, 0) - d(uz, 2)
+    wz = d(uy, 2) - d(ux, 1)
+    return float((0.5 * (wx ** 2 + wy ** 2 + wz ** 2)).mean())

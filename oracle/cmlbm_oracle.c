@@ -1,0 +1,643 @@
+/*
+ * cmlbm_oracle.c -- TEST INFRASTRUCTURE ONLY (see cmlbm_oracle.h).
+ *
+ * Plain FP64 restatement of the D3Q27 central-moment LBM with forcing of
+ * De Rosis, Huang & Coreixas, "Three-dimensional central-moments-based lattice
+ * Boltzmann method with external forcing" (arXiv 1905.10182).  Every function cites
+ * the section / equation it follows.  Nothing here is blocked, fused or reordered
+ * beyond what those equations state; speed is not a goal.
+ */
+#include "cmlbm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define Q ORC_Q
+static const double CS2 = 1.0 / 3.0; /* c_s^2, Sec. II below Eq. eq:truncation */
+
+/* ---------------------------------------------------------------- lattice (Sec. II) */
+/* |c_ix>, |c_iy>, |c_iz> in the order printed at the start of Sec. II. */
+static const int CX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
+static const int CY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, 1, -1, -1, 1, 1, -1, -1};
+static const int CZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 1, 1, 1, 1, -1, -1, -1, -1};
+
+void orc_velocities(int c[Q * 3]) {
+    for (int i = 0; i < Q; ++i) {
+        c[3 * i + 0] = CX[i];
+        c[3 * i + 1] = CY[i];
+        c[3 * i + 2] = CZ[i];
+    }
+}
+
+/* w_0 = 8/27, w_{1..6} = 2/27, w_{7..18} = 1/54, w_{19..26} = 1/216 (Sec. II, below Eq. eq:truncation) */
+static double weight(int i) {
+    if (i == 0) return 8.0 / 27.0;
+    if (i <= 6) return 2.0 / 27.0;
+    if (i <= 18) return 1.0 / 54.0;
+    return 1.0 / 216.0;
+}
+
+void orc_weights(double w[Q]) {
+    for (int i = 0; i < Q; ++i) w[i] = weight(i);
+}
+
+/* the direction with c_j = -c_i, found by search */
+int orc_opposite(int i) {
+    for (int j = 0; j < Q; ++j)
+        if (CX[j] == -CX[i] && CY[j] == -CY[i] && CZ[j] == -CZ[i]) return j;
+    return -1;
+}
+
+/* ------------------------------------------------------- Hermite polynomials (App. A) */
+/* 1D discrete Hermite polynomials of degree 0..2 (App. A): 1, c, c^2 - c_s^2 */
+static double hermite1d(int n, double c) {
+    if (n == 0) return 1.0;
+    if (n == 1) return c;
+    return c * c - CS2;
+}
+
+/* Eq. eq:HermiteTensorProduct: H_{x..x y..y z..z} = H^(nx)(c_x) H^(ny)(c_y) H^(nz)(c_z) */
+double orc_hermite(int i, int nx, int ny, int nz) {
+    return hermite1d(nx, CX[i]) * hermite1d(ny, CY[i]) * hermite1d(nz, CZ[i]);
+}
+
+static double factorial(int n) { return n == 2 ? 2.0 : 1.0; } /* n in {0, 1, 2} */
+
+static double ipow(double v, int n) {
+    double r = 1.0;
+    for (int k = 0; k < n; ++k) r *= v;
+    return r;
+}
+
+/* --------------------------------------------------------- equilibrium, Eq. eq:truncation
+ * f_i^eq = w_i rho sum over the 27 tensors H_{nx ny nz} (nx, ny, nz in 0..2, at most two per
+ * axis, App. A) of H_{nx ny nz}(c_i) ux^nx uy^ny uz^nz / (nx! ny! nz! c_s^(2n)), n = nx+ny+nz:
+ * the coefficient rule stated right after Eq. eq:truncation.  order < 6 drops tensors with
+ * n > order (order 2 = the classical second-order equilibrium). */
+void orc_equilibrium(double rho, const double u[3], int order, double feq[Q]) {
+    for (int i = 0; i < Q; ++i) {
+        double s = 0.0;
+        for (int nz = 0; nz <= 2; ++nz)
+            for (int ny = 0; ny <= 2; ++ny)
+                for (int nx = 0; nx <= 2; ++nx) {
+                    int n = nx + ny + nz;
+                    if (n > order) continue;
+                    double coef = 1.0 / (factorial(nx) * factorial(ny) * factorial(nz) * ipow(CS2, n));
+                    s += coef * orc_hermite(i, nx, ny, nz) * ipow(u[0], nx) * ipow(u[1], ny) * ipow(u[2], nz);
+                }
+        feq[i] = weight(i) * rho * s;
+    }
+}
+
+/* ------------------------------------------------------------ forcing term, Eq. forcing
+ * Eq. generalForcing: F_i = w_i sum_n (1/n!) [F u^(n-1)] . H^(n).  For the tensor H_{nx ny nz}
+ * the cyclic bracket [F u..u] contracts to the derivative of ux^nx uy^ny uz^nz along F:
+ *   Fx nx ux^(nx-1) uy^ny uz^nz + Fy ny ux^nx uy^(ny-1) uz^nz + Fz nz ux^nx uy^ny uz^(nz-1),
+ * which is exactly each bracket printed in Eq. forcing (e.g. H_xxy: 2 ux uy Fx + ux^2 Fy), with
+ * the same coefficients 1/(nx! ny! nz! c_s^(2n)) as the equilibrium.
+ * Reading: F is a force density and the printed rho prefactor is not applied, so that
+ * sum_i F_i c_i = F, consistent with R_1 = F_x (Eq. force_cms_sixth) and Eq. macroscopic. */
+void orc_forcing_term(const double F[3], const double u[3], int order, double Fi[Q]) {
+    for (int i = 0; i < Q; ++i) {
+        double s = 0.0;
+        for (int nz = 0; nz <= 2; ++nz)
+            for (int ny = 0; ny <= 2; ++ny)
+                for (int nx = 0; nx <= 2; ++nx) {
+                    int n = nx + ny + nz;
+                    if (n == 0 || n > order) continue;
+                    double coef = 1.0 / (factorial(nx) * factorial(ny) * factorial(nz) * ipow(CS2, n));
+                    double bracket = 0.0;
+                    if (nx > 0) bracket += F[0] * nx * ipow(u[0], nx - 1) * ipow(u[1], ny) * ipow(u[2], nz);
+                    if (ny > 0) bracket += F[1] * ny * ipow(u[0], nx) * ipow(u[1], ny - 1) * ipow(u[2], nz);
+                    if (nz > 0) bracket += F[2] * nz * ipow(u[0], nx) * ipow(u[1], ny) * ipow(u[2], nz - 1);
+                    s += coef * orc_hermite(i, nx, ny, nz) * bracket;
+                }
+        Fi[i] = weight(i) * s;
+    }
+}
+
+/* ------------------------------------------------------------ CM basis, Eq. basis
+ * Each T_j is a signed sum of monomials cbx^a cby^b cbz^c (cb = c - u, Eq. central_directions),
+ * transcribed from Eq. basis.  Monomial (a, b, c) is encoded as a + 3b + 9c. */
+typedef struct { int n; int sign[3]; int mono[3]; } basis_row;
+#define M(a, b, c) ((a) + 3 * (b) + 9 * (c))
+static const basis_row BASIS[Q] = {
+    {1, {1}, {M(0, 0, 0)}},                                   /* T0  = 1                          */
+    {1, {1}, {M(1, 0, 0)}},                                   /* T1  = cbx                        */
+    {1, {1}, {M(0, 1, 0)}},                                   /* T2  = cby                        */
+    {1, {1}, {M(0, 0, 1)}},                                   /* T3  = cbz                        */
+    {1, {1}, {M(1, 1, 0)}},                                   /* T4  = cbx cby                    */
+    {1, {1}, {M(1, 0, 1)}},                                   /* T5  = cbx cbz                    */
+    {1, {1}, {M(0, 1, 1)}},                                   /* T6  = cby cbz                    */
+    {2, {1, -1}, {M(2, 0, 0), M(0, 2, 0)}},                   /* T7  = cbx^2 - cby^2              */
+    {2, {1, -1}, {M(2, 0, 0), M(0, 0, 2)}},                   /* T8  = cbx^2 - cbz^2              */
+    {3, {1, 1, 1}, {M(2, 0, 0), M(0, 2, 0), M(0, 0, 2)}},     /* T9  = cbx^2 + cby^2 + cbz^2      */
+    {2, {1, 1}, {M(1, 2, 0), M(1, 0, 2)}},                    /* T10 = cbx cby^2 + cbx cbz^2      */
+    {2, {1, 1}, {M(2, 1, 0), M(0, 1, 2)}},                    /* T11 = cbx^2 cby + cby cbz^2      */
+    {2, {1, 1}, {M(2, 0, 1), M(0, 2, 1)}},                    /* T12 = cbx^2 cbz + cby^2 cbz      */
+    {2, {1, -1}, {M(1, 2, 0), M(1, 0, 2)}},                   /* T13 = cbx cby^2 - cbx cbz^2      */
+    {2, {1, -1}, {M(2, 1, 0), M(0, 1, 2)}},                   /* T14 = cbx^2 cby - cby cbz^2      */
+    {2, {1, -1}, {M(2, 0, 1), M(0, 2, 1)}},                   /* T15 = cbx^2 cbz - cby^2 cbz      */
+    {1, {1}, {M(1, 1, 1)}},                                   /* T16 = cbx cby cbz                */
+    {3, {1, 1, 1}, {M(2, 2, 0), M(2, 0, 2), M(0, 2, 2)}},     /* T17 = x2y2 + x2z2 + y2z2         */
+    {3, {1, 1, -1}, {M(2, 2, 0), M(2, 0, 2), M(0, 2, 2)}},    /* T18 = x2y2 + x2z2 - y2z2         */
+    {2, {1, -1}, {M(2, 2, 0), M(2, 0, 2)}},                   /* T19 = x2y2 - x2z2                */
+    {1, {1}, {M(2, 1, 1)}},                                   /* T20 = cbx^2 cby cbz              */
+    {1, {1}, {M(1, 2, 1)}},                                   /* T21 = cbx cby^2 cbz              */
+    {1, {1}, {M(1, 1, 2)}},                                   /* T22 = cbx cby cbz^2              */
+    {1, {1}, {M(1, 2, 2)}},                                   /* T23 = cbx cby^2 cbz^2            */
+    {1, {1}, {M(2, 1, 2)}},                                   /* T24 = cbx^2 cby cbz^2            */
+    {1, {1}, {M(2, 2, 1)}},                                   /* T25 = cbx^2 cby^2 cbz            */
+    {1, {1}, {M(2, 2, 2)}},                                   /* T26 = cbx^2 cby^2 cbz^2          */
+};
+#undef M
+
+static double monomial(int m, double bx, double by, double bz) {
+    return ipow(bx, m % 3) * ipow(by, (m / 3) % 3) * ipow(bz, m / 9);
+}
+
+void orc_basis(const double u[3], double T[Q * Q]) {
+    for (int i = 0; i < Q; ++i) {
+        double bx = CX[i] - u[0], by = CY[i] - u[1], bz = CZ[i] - u[2]; /* Eq. central_directions */
+        for (int j = 0; j < Q; ++j) {
+            double v = 0.0;
+            for (int t = 0; t < BASIS[j].n; ++t) v += BASIS[j].sign[t] * monomial(BASIS[j].mono[t], bx, by, bz);
+            T[i * Q + j] = v;
+        }
+    }
+}
+
+void orc_central_moments(const double u[3], const double v[Q], double k[Q]) {
+    double T[Q * Q];
+    orc_basis(u, T);
+    for (int j = 0; j < Q; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < Q; ++i) s += T[i * Q + j] * v[i];
+        k[j] = s;
+    }
+}
+
+/* Gaussian elimination with partial pivoting: solves A x = b, A is n x n row-major (destroyed). */
+static int gauss_solve(int n, double* A, double* b, double* x) {
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (fabs(A[r * n + col]) > fabs(A[piv * n + col])) piv = r;
+        if (A[piv * n + col] == 0.0) return ORC_ERR_SINGULAR;
+        if (piv != col) {
+            for (int c = 0; c < n; ++c) {
+                double t = A[col * n + c];
+                A[col * n + c] = A[piv * n + c];
+                A[piv * n + c] = t;
+            }
+            double t = b[col];
+            b[col] = b[piv];
+            b[piv] = t;
+        }
+        for (int r = col + 1; r < n; ++r) {
+            double m = A[r * n + col] / A[col * n + col];
+            if (m == 0.0) continue;
+            for (int c = col; c < n; ++c) A[r * n + c] -= m * A[col * n + c];
+            b[r] -= m * b[col];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = b[r];
+        for (int c = r + 1; c < n; ++c) s -= A[r * n + c] * x[c];
+        x[r] = s / A[r * n + r];
+    }
+    return ORC_OK;
+}
+
+/* Eq. system: f* = (T^T)^-1 k*, solved literally */
+int orc_inverse_literal(const double u[3], const double k[Q], double v[Q]) {
+    double T[Q * Q], A[Q * Q], b[Q];
+    orc_basis(u, T);
+    for (int j = 0; j < Q; ++j) {
+        for (int i = 0; i < Q; ++i) A[j * Q + i] = T[i * Q + j]; /* A = T^T */
+        b[j] = k[j];
+    }
+    return gauss_solve(Q, A, b, v);
+}
+
+/* ------------------------------------------------------------ fast CM inverse
+ * The fast CM transform the paper cites after Eq. system: T^T factors into (i) a constant map
+ * B from the 27 monomial central moments kappa_abc to the basis k (read off Eq. basis) and
+ * (ii) the shifted-monomial transform, a tensor product of three D1Q3 transforms.  Inverting:
+ * kappa = B^-1 k, then along each axis central moments -> raw moments (binomial expansion of
+ * c^n = (cb + u)^n) -> the three populations c = -1, 0, +1 (sum f = M0, sum c f = M1,
+ * sum c^2 f = M2). */
+static double BINV[Q * Q];
+static int binv_ready = 0;
+
+static void init_binv(void) {
+    if (binv_ready) return;
+    double B[Q * Q], e[Q], col[Q];
+    for (int j = 0; j < Q; ++j)
+        for (int m = 0; m < Q; ++m) B[j * Q + m] = 0.0;
+    for (int j = 0; j < Q; ++j)
+        for (int t = 0; t < BASIS[j].n; ++t) B[j * Q + BASIS[j].mono[t]] += BASIS[j].sign[t];
+    for (int c = 0; c < Q; ++c) {
+        double A[Q * Q];
+        memcpy(A, B, sizeof(A));
+        for (int r = 0; r < Q; ++r) e[r] = (r == c) ? 1.0 : 0.0;
+        gauss_solve(Q, A, e, col);
+        for (int r = 0; r < Q; ++r) BINV[r * Q + c] = col[r];
+    }
+    binv_ready = 1;
+}
+
+/* D1Q3: central moments (m0, m1, m2) at shift u -> populations p[0] (c=-1), p[1] (c=0), p[2] (c=+1) */
+static void d1q3_inverse(double m0, double m1, double m2, double u, double p[3]) {
+    double M0 = m0;
+    double M1 = m1 + u * m0;
+    double M2 = m2 + 2.0 * u * m1 + u * u * m0;
+    p[1] = M0 - M2;
+    p[2] = 0.5 * (M1 + M2);
+    p[0] = 0.5 * (M2 - M1);
+}
+
+void orc_inverse_fast(const double u[3], const double k[Q], double v[Q]) {
+    init_binv();
+    double kap[Q];
+    for (int m = 0; m < Q; ++m) {
+        double s = 0.0;
+        for (int j = 0; j < Q; ++j) s += BINV[m * Q + j] * k[j];
+        kap[m] = s;
+    }
+    /* A[a][b][c]: moment orders a, b, c replaced one axis at a time by velocity index (c+1) */
+    double A[3][3][3], p[3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 3; ++c) A[a][b][c] = kap[a + 3 * b + 9 * c];
+    for (int a = 0; a < 3; ++a) /* z */
+        for (int b = 0; b < 3; ++b) {
+            d1q3_inverse(A[a][b][0], A[a][b][1], A[a][b][2], u[2], p);
+            for (int c = 0; c < 3; ++c) A[a][b][c] = p[c];
+        }
+    for (int a = 0; a < 3; ++a) /* y */
+        for (int c = 0; c < 3; ++c) {
+            d1q3_inverse(A[a][0][c], A[a][1][c], A[a][2][c], u[1], p);
+            for (int b = 0; b < 3; ++b) A[a][b][c] = p[b];
+        }
+    for (int b = 0; b < 3; ++b) /* x */
+        for (int c = 0; c < 3; ++c) {
+            d1q3_inverse(A[0][b][c], A[1][b][c], A[2][b][c], u[0], p);
+            for (int a = 0; a < 3; ++a) A[a][b][c] = p[a];
+        }
+    for (int i = 0; i < Q; ++i) v[i] = A[CX[i] + 1][CY[i] + 1][CZ[i] + 1];
+}
+
+/* ------------------------------------------------------------ collision */
+/* Eq. macroscopic */
+static void macroscopic_node(const double f[Q], const double F[3], double* rho, double u[3]) {
+    double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        r += f[i];
+        jx += f[i] * CX[i];
+        jy += f[i] * CY[i];
+        jz += f[i] * CZ[i];
+    }
+    *rho = r;
+    u[0] = (jx + 0.5 * F[0]) / r;
+    u[1] = (jy + 0.5 * F[1]) / r;
+    u[2] = (jz + 0.5 * F[2]) / r;
+}
+
+/* Eq. eq:relaxationMatrix: Lambda = diag[1,1,1,1, w,w,w,w,w, 1,...,1] */
+static void paper_lambda(double omega, double L[Q]) {
+    for (int j = 0; j < Q; ++j) L[j] = (j >= 4 && j <= 8) ? omega : 1.0;
+}
+
+/* The definition (Sec. II, CMs with forcing):
+ *   k* = (I - L) T^T f + L T^T feq + (I - L/2) T^T F_i,   f* = (T^T)^-1 k*  (Eq. system) */
+static int collide_literal(const orc_desc* d, const double f[Q], const double F[3], double fs[Q]) {
+    double rho, u[3], L[Q], feq[Q], Fi[Q], k[Q], keq[Q], R[Q], ks[Q];
+    macroscopic_node(f, F, &rho, u);
+    if (d->lambda) memcpy(L, d->lambda, sizeof(L));
+    else paper_lambda(d->omega, L);
+    orc_equilibrium(rho, u, d->eq_order, feq);
+    orc_forcing_term(F, u, d->force_order, Fi);
+    orc_central_moments(u, f, k);
+    orc_central_moments(u, feq, keq);
+    orc_central_moments(u, Fi, R);
+    for (int j = 0; j < Q; ++j) ks[j] = (1.0 - L[j]) * k[j] + L[j] * keq[j] + (1.0 - 0.5 * L[j]) * R[j];
+    return orc_inverse_literal(u, ks, fs);
+}
+
+/* Eq. collision: f* = f + w (feq - f) + (1 - w/2) F_i, complete feq and F_i */
+static void collide_bgk(const orc_desc* d, const double f[Q], const double F[3], double fs[Q]) {
+    double rho, u[3], feq[Q], Fi[Q];
+    double w = d->lambda ? d->lambda[0] : d->omega;
+    macroscopic_node(f, F, &rho, u);
+    orc_equilibrium(rho, u, 6, feq);
+    orc_forcing_term(F, u, 6, Fi);
+    for (int i = 0; i < Q; ++i) fs[i] = f[i] + w * (feq[i] - f[i]) + (1.0 - 0.5 * w) * Fi[i];
+}
+
+/* The five-step time iteration summarised at the end of Sec. II, steps 1-4:
+ *   1. rho, u (Eq. macroscopic);  2. k4..k8 (Eq. pre_collision);
+ *   3. post-collision CMs (Eq. post_collision_central_moments_forcing);
+ *   4. f* = (T^T)^-1 k* (Eq. system) through the fast CM transform. */
+static void collide_paper(const orc_desc* d, const double f[Q], const double F[3], double fs[Q]) {
+    double rho, u[3], ks[Q];
+    macroscopic_node(f, F, &rho, u);
+    double k4 = 0, k5 = 0, k6 = 0, k7 = 0, k8 = 0;
+    for (int i = 0; i < Q; ++i) {
+        double bx = CX[i] - u[0], by = CY[i] - u[1], bz = CZ[i] - u[2];
+        k4 += f[i] * bx * by;
+        k5 += f[i] * bx * bz;
+        k6 += f[i] * by * bz;
+        k7 += f[i] * (bx * bx - by * by);
+        k8 += f[i] * (bx * bx - bz * bz);
+    }
+    double w = d->omega;
+    for (int j = 0; j < Q; ++j) ks[j] = 0.0;
+    ks[0] = rho;
+    ks[1] = 0.5 * F[0];
+    ks[2] = 0.5 * F[1];
+    ks[3] = 0.5 * F[2];
+    ks[4] = (1.0 - w) * k4;
+    ks[5] = (1.0 - w) * k5;
+    ks[6] = (1.0 - w) * k6;
+    ks[7] = (1.0 - w) * k7;
+    ks[8] = (1.0 - w) * k8;
+    ks[9] = 3.0 * rho * CS2;
+    ks[10] = F[0] * CS2;
+    ks[11] = F[1] * CS2;
+    ks[12] = F[2] * CS2;
+    ks[17] = rho * CS2;
+    ks[18] = rho * CS2 * CS2;
+    ks[23] = 0.5 * F[0] * CS2 * CS2;
+    ks[24] = 0.5 * F[1] * CS2 * CS2;
+    ks[25] = 0.5 * F[2] * CS2 * CS2;
+    ks[26] = rho * CS2 * CS2 * CS2;
+    orc_inverse_fast(u, ks, fs);
+}
+
+int orc_collide(const orc_desc* d, const double f[Q], const double F[3], double fs[Q]) {
+    init_binv();
+    switch (d->collision) {
+    case ORC_COLL_LITERAL: return collide_literal(d, f, F, fs);
+    case ORC_COLL_PAPER: collide_paper(d, f, F, fs); return ORC_OK;
+    case ORC_COLL_BGK: collide_bgk(d, f, F, fs); return ORC_OK;
+    case ORC_COLL_NONE: memcpy(fs, f, sizeof(double) * Q); return ORC_OK;
+    default: return ORC_ERR_ARG;
+    }
+}
+
+/* ------------------------------------------------------------ grid */
+typedef struct { long long N; } gridinfo;
+
+static long long node_index(const orc_desc* d, int x, int y, int z) {
+    return (long long)x + (long long)d->nx * ((long long)y + (long long)d->ny * z);
+}
+
+static int is_solid(const orc_desc* d, long long n) { return d->mask && d->mask[n]; }
+
+/* Neighbour x + s*c_i with periodic wrap (x, z, and y without walls).
+ * Returns -1 when the link leaves through a y wall or ends on a solid node. */
+static long long neighbour(const orc_desc* d, int x, int y, int z, int i, int s) {
+    int xn = x + s * CX[i], yn = y + s * CY[i], zn = z + s * CZ[i];
+    xn = (xn % d->nx + d->nx) % d->nx;
+    zn = (zn % d->nz + d->nz) % d->nz;
+    if (d->walls_y) {
+        if (yn < 0 || yn >= d->ny) return -1;
+    } else {
+        yn = (yn % d->ny + d->ny) % d->ny;
+    }
+    long long m = node_index(d, xn, yn, zn);
+    if (is_solid(d, m)) return -1;
+    return m;
+}
+
+static void gather_node(const double* f, long long N, long long n, double out[Q]) {
+    for (int i = 0; i < Q; ++i) out[i] = f[(long long)i * N + n];
+}
+
+/* psi = 1 - exp(-rho) of the static-droplet test (Sec. III) */
+static void compute_psi(const orc_desc* d, const double* f, double* psi) {
+    long long N = (long long)d->nx * d->ny * d->nz;
+#pragma omp parallel for schedule(static)
+    for (long long n = 0; n < N; ++n) {
+        double r = 0.0;
+        for (int i = 0; i < Q; ++i) r += f[(long long)i * N + n];
+        psi[n] = 1.0 - exp(-r);
+    }
+}
+
+/* Force density at node n. */
+static void node_force(const orc_desc* d, const double* psi, int x, int y, int z, double F[3]) {
+    long long n = node_index(d, x, y, z);
+    F[0] = F[1] = F[2] = 0.0;
+    switch (d->force_kind) {
+    case ORC_FORCE_UNIFORM:
+        F[0] = d->force[0];
+        F[1] = d->force[1];
+        F[2] = d->force[2];
+        break;
+    case ORC_FORCE_KOLMOGOROV:
+        F[0] = d->force[0] * sin(2.0 * M_PI * (double)y / (double)d->ny);
+        break;
+    case ORC_FORCE_FIELD:
+        F[0] = d->fx[n];
+        F[1] = d->fy[n];
+        F[2] = d->fz[n];
+        break;
+    case ORC_FORCE_SHAN_CHEN: {
+        /* F = -G psi(x) sum_i w_i c_i psi(x + c_i), periodic (Sec. III, static droplet) */
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            long long m = neighbour(d, x, y, z, i, +1);
+            double w = weight(i);
+            sx += w * CX[i] * psi[m];
+            sy += w * CY[i] * psi[m];
+            sz += w * CZ[i] * psi[m];
+        }
+        F[0] = -d->G * psi[n] * sx;
+        F[1] = -d->G * psi[n] * sy;
+        F[2] = -d->G * psi[n] * sz;
+        break;
+    }
+    default: break;
+    }
+}
+
+static int check_desc(const orc_desc* d) {
+    if (!d || d->nx <= 0 || d->ny <= 0 || d->nz <= 0) return ORC_ERR_ARG;
+    if (d->force_kind == ORC_FORCE_SHAN_CHEN && (d->walls_y || d->mask)) return ORC_ERR_ARG;
+    if (d->force_kind == ORC_FORCE_FIELD && (!d->fx || !d->fy || !d->fz)) return ORC_ERR_ARG;
+    if (d->collision < 0 || d->collision > ORC_COLL_NONE) return ORC_ERR_ARG;
+    if (d->threads > 0) {
+#ifdef _OPENMP
+        omp_set_num_threads(d->threads);
+#endif
+    }
+    init_binv();
+    return ORC_OK;
+}
+
+int orc_force_field(const orc_desc* d, const double* f, double* F3) {
+    int st = check_desc(d);
+    if (st) return st;
+    long long N = (long long)d->nx * d->ny * d->nz;
+    double* psi = NULL;
+    if (d->force_kind == ORC_FORCE_SHAN_CHEN) {
+        psi = (double*)malloc(sizeof(double) * N);
+        if (!psi) return ORC_ERR_NOMEM;
+        compute_psi(d, f, psi);
+    }
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < d->nz; ++z)
+        for (int y = 0; y < d->ny; ++y)
+            for (int x = 0; x < d->nx; ++x) {
+                long long n = node_index(d, x, y, z);
+                double F[3];
+                node_force(d, psi, x, y, z, F);
+                F3[n] = F[0];
+                F3[N + n] = F[1];
+                F3[2 * N + n] = F[2];
+            }
+    free(psi);
+    return ORC_OK;
+}
+
+int orc_macroscopic(const orc_desc* d, const double* f, double* rho, double* u3) {
+    long long N = (long long)d->nx * d->ny * d->nz;
+    double* F3 = (double*)malloc(sizeof(double) * 3 * N);
+    if (!F3) return ORC_ERR_NOMEM;
+    int st = orc_force_field(d, f, F3);
+    if (st) {
+        free(F3);
+        return st;
+    }
+#pragma omp parallel for schedule(static)
+    for (long long n = 0; n < N; ++n) {
+        double fl[Q], F[3] = {F3[n], F3[N + n], F3[2 * N + n]}, r, u[3];
+        gather_node(f, N, n, fl);
+        macroscopic_node(fl, F, &r, u);
+        rho[n] = r;
+        u3[n] = u[0];
+        u3[N + n] = u[1];
+        u3[2 * N + n] = u[2];
+    }
+    free(F3);
+    return ORC_OK;
+}
+
+int orc_init_equilibrium(const orc_desc* d, const double* rho, const double* u3, double* f) {
+    int st = check_desc(d);
+    if (st) return st;
+    long long N = (long long)d->nx * d->ny * d->nz;
+#pragma omp parallel for schedule(static)
+    for (long long n = 0; n < N; ++n) {
+        double feq[Q], u[3] = {u3[n], u3[N + n], u3[2 * N + n]}, r = rho[n];
+        if (is_solid(d, n)) {
+            u[0] = u[1] = u[2] = 0.0;
+            r = d->rho0;
+        }
+        orc_equilibrium(r, u, 6, feq);
+        for (int i = 0; i < Q; ++i) f[(long long)i * N + n] = feq[i];
+    }
+    return ORC_OK;
+}
+
+/* Eq. streaming, f_i(x + c_i, t+1) = f*_i(x, t), written as a pull from x - c_i; a link whose
+ * source lies behind a wall or on a solid node takes the bounced-back population f*_opp(i)(x, t)
+ * (halfway bounce-back). */
+int orc_step(const orc_desc* d, double* f, int nsteps) {
+    int st = check_desc(d);
+    if (st) return st;
+    long long N = (long long)d->nx * d->ny * d->nz;
+    double* fs = (double*)malloc(sizeof(double) * Q * N);
+    double* psi = (d->force_kind == ORC_FORCE_SHAN_CHEN) ? (double*)malloc(sizeof(double) * N) : NULL;
+    if (!fs || (d->force_kind == ORC_FORCE_SHAN_CHEN && !psi)) {
+        free(fs);
+        free(psi);
+        return ORC_ERR_NOMEM;
+    }
+    int err = ORC_OK;
+    for (int s = 0; s < nsteps && !err; ++s) {
+        if (psi) compute_psi(d, f, psi);
+#pragma omp parallel for schedule(static) reduction(| : err)
+        for (int z = 0; z < d->nz; ++z)
+            for (int y = 0; y < d->ny; ++y)
+                for (int x = 0; x < d->nx; ++x) {
+                    long long n = node_index(d, x, y, z);
+                    double fl[Q], fo[Q], F[3];
+                    gather_node(f, N, n, fl);
+                    if (is_solid(d, n)) {
+                        for (int i = 0; i < Q; ++i) fs[(long long)i * N + n] = fl[i];
+                        continue;
+                    }
+                    node_force(d, psi, x, y, z, F);
+                    err |= orc_collide(d, fl, F, fo);
+                    for (int i = 0; i < Q; ++i) fs[(long long)i * N + n] = fo[i];
+                }
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < d->nz; ++z)
+            for (int y = 0; y < d->ny; ++y)
+                for (int x = 0; x < d->nx; ++x) {
+                    long long n = node_index(d, x, y, z);
+                    if (is_solid(d, n)) continue;
+                    for (int i = 0; i < Q; ++i) {
+                        long long src = neighbour(d, x, y, z, i, -1);
+                        f[(long long)i * N + n] = (src >= 0) ? fs[(long long)i * N + src]
+                                                             : fs[(long long)orc_opposite(i) * N + n];
+                    }
+                }
+    }
+    free(fs);
+    free(psi);
+    return err;
+}
+
+int orc_step_sampled(const orc_desc* d, const double* f, const long long* nodes, int count, double* out) {
+    int st = check_desc(d);
+    if (st) return st;
+    long long N = (long long)d->nx * d->ny * d->nz;
+    double* psi = NULL;
+    if (d->force_kind == ORC_FORCE_SHAN_CHEN) {
+        psi = (double*)malloc(sizeof(double) * N);
+        if (!psi) return ORC_ERR_NOMEM;
+        compute_psi(d, f, psi);
+    }
+    int err = ORC_OK;
+#pragma omp parallel for schedule(dynamic) reduction(| : err)
+    for (int k = 0; k < count; ++k) {
+        long long n = nodes[k];
+        int x = (int)(n % d->nx), y = (int)((n / d->nx) % d->ny), z = (int)(n / ((long long)d->nx * d->ny));
+        double fl[Q], fo[Q], F[3];
+        if (is_solid(d, n)) {
+            gather_node(f, N, n, fl);
+            for (int i = 0; i < Q; ++i) out[(long long)k * Q + i] = fl[i];
+            continue;
+        }
+        for (int i = 0; i < Q; ++i) {
+            long long src = neighbour(d, x, y, z, i, -1);
+            int dir = i;
+            long long at = src;
+            int sx = x - CX[i], sy = y - CY[i], sz = z - CZ[i];
+            if (src < 0) { /* bounce-back: f*_opp(i) of this node */
+                dir = orc_opposite(i);
+                at = n;
+                sx = x;
+                sy = y;
+                sz = z;
+            }
+            sx = (sx % d->nx + d->nx) % d->nx;
+            sy = (sy % d->ny + d->ny) % d->ny;
+            sz = (sz % d->nz + d->nz) % d->nz;
+            gather_node(f, N, at, fl);
+            node_force(d, psi, sx, sy, sz, F);
+            err |= orc_collide(d, fl, F, fo);
+            out[(long long)k * Q + i] = fo[dir];
+        }
+    }
+    free(psi);
+    return err;
+}

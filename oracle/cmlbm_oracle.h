@@ -1,0 +1,106 @@
+/*
+ * cmlbm_oracle.h -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow FP64 CPU restatement of the D3Q27 central-moment lattice Boltzmann
+ * scheme with external forcing of De Rosis, Huang & Coreixas (arXiv 1905.10182).
+ * It exists to check the CUDA path.  Only the test suite, the smoke entry point and
+ * the benchmark's CPU-baseline leg may load it; the product library never does.
+ * It shares no code, header, table or constant with the CUDA path.
+ *
+ * Conventions
+ *   - Population i of node n = x + nx*(y + ny*z) is f[i*N + n], N = nx*ny*nz
+ *     (structure of arrays, x fastest), values are full populations f_i (not
+ *     deviations), FP64.
+ *   - Lattice units; c_s^2 = 1/3 (Sec. II, below Eq. eq:truncation).
+ *   - Force F is a force density: the forcing term carries no rho prefactor
+ *     (reading of Eq. forcing that reproduces Eq. force_cms_sixth and Eq. macroscopic).
+ */
+#ifndef CMLBM_ORACLE_H
+#define CMLBM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_Q 27
+
+/* collision operators */
+enum {
+    ORC_COLL_LITERAL = 0, /* k* = (I-L)T^T f + L T^T feq + (I-L/2) T^T F, f* = (T^T)^-1 k*   (Sec. II) */
+    ORC_COLL_PAPER   = 1, /* five-step summary of Sec. II: closed-form post-collision CMs + fast CM inverse */
+    ORC_COLL_BGK     = 2, /* single-rate BGK, Eq. collision */
+    ORC_COLL_NONE    = 3  /* identity: pure streaming, used to label populations and check indices */
+};
+
+/* force sources */
+enum {
+    ORC_FORCE_NONE = 0,
+    ORC_FORCE_UNIFORM = 1,    /* F = (force[0], force[1], force[2]) everywhere                   */
+    ORC_FORCE_KOLMOGOROV = 2, /* F_x = force[0] * sin(2 pi y / ny), F_y = F_z = 0                */
+    ORC_FORCE_FIELD = 3,      /* F from fx, fy, fz arrays (N each)                               */
+    ORC_FORCE_SHAN_CHEN = 4   /* F = -G psi(x) sum_i w_i c_i psi(x + c_i), psi = 1 - exp(-rho)  (Sec. III, static droplet) */
+};
+
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_SINGULAR = 2, ORC_ERR_NOMEM = 3 };
+
+typedef struct {
+    int nx, ny, nz;
+    double omega;               /* rate of the second-order moments k4..k8, Eq. eq:relaxationMatrix */
+    double rho0;                /* reference density, used only by orc_init_rest */
+    int walls_y;                /* 1: halfway bounce-back walls at y = -1/2 and y = ny - 1/2 */
+    const unsigned char* mask;  /* NULL or N bytes, 1 = solid node */
+    int collision;              /* ORC_COLL_* */
+    int eq_order;               /* Hermite order kept in feq   (LITERAL only; 6 = complete, Eq. eq:truncation) */
+    int force_order;            /* Hermite order kept in F_i   (LITERAL only; 6 = complete, Eq. forcing)       */
+    const double* lambda;       /* LITERAL/BGK override: 27 relaxation rates, NULL = paper's Lambda */
+    int force_kind;             /* ORC_FORCE_* */
+    double force[3];
+    double G;                   /* Shan-Chen interaction strength */
+    const double* fx;
+    const double* fy;
+    const double* fz;
+    int threads;                /* OpenMP threads, <= 0 = runtime default */
+} orc_desc;
+
+/* lattice (Sec. II): velocities in the paper's order, weights, opposite direction */
+void orc_velocities(int c[ORC_Q * 3]);
+void orc_weights(double w[ORC_Q]);
+int orc_opposite(int i);
+
+/* Hermite tensor H_{nx ny nz}(c_i) of App. A (tensor product of 1D polynomials) */
+double orc_hermite(int i, int nx, int ny, int nz);
+
+/* Eq. eq:truncation, keeping Hermite tensors of total order <= order (6 = complete) */
+void orc_equilibrium(double rho, const double u[3], int order, double feq[ORC_Q]);
+/* Eq. forcing / Eq. generalForcing, keeping Hermite tensors of total order <= order (6 = complete) */
+void orc_forcing_term(const double F[3], const double u[3], int order, double Fi[ORC_Q]);
+/* Eq. basis: T[i*27 + j] = T_j evaluated at the shifted velocity c_i - u */
+void orc_basis(const double u[3], double T[ORC_Q * ORC_Q]);
+/* k = T^T v (central moments of any population-space vector) */
+void orc_central_moments(const double u[3], const double v[ORC_Q], double k[ORC_Q]);
+/* solve (T^T) v = k for v: the literal inverse of Eq. system */
+int orc_inverse_literal(const double u[3], const double k[ORC_Q], double v[ORC_Q]);
+/* the same inverse through the fast CM transform (three 1D D1Q3 inverses) */
+void orc_inverse_fast(const double u[3], const double k[ORC_Q], double v[ORC_Q]);
+
+/* One node's collision; F is the force density at the node. */
+int orc_collide(const orc_desc* d, const double f[ORC_Q], const double F[3], double fstar[ORC_Q]);
+
+/* Macroscopic fields of Eq. macroscopic (u includes F/2). rho: N, u: 3N (ux block, uy, uz). */
+int orc_force_field(const orc_desc* d, const double* f, double* F3);
+int orc_macroscopic(const orc_desc* d, const double* f, double* rho, double* u3);
+
+/* f = feq(rho, u) (complete equilibrium) on every fluid node; solid nodes get feq(rho0, 0). */
+int orc_init_equilibrium(const orc_desc* d, const double* rho, const double* u3, double* f);
+
+/* nsteps of collide (Eq. collision / Sec. II) + two-array streaming (Eq. streaming) with
+   halfway bounce-back at walls and solid nodes; f is updated in place. */
+int orc_step(const orc_desc* d, double* f, int nsteps);
+
+/* One step evaluated only at the listed nodes: out[k*27 + i] = f_i(nodes[k], t+1). */
+int orc_step_sampled(const orc_desc* d, const double* f, const long long* nodes, int count, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
