@@ -1,0 +1,170 @@
+/*
+ * cmlbm.h -- C ABI of the GB300 (sm_103a) D3Q27 central-moment lattice Boltzmann solver with
+ * external forcing of De Rosis, Huang & Coreixas, "Three-dimensional central-moments-based
+ * lattice Boltzmann method with external forcing" (arXiv 1905.10182).
+ *
+ * What one step computes (Sec. II, the five-step time iteration at its end):
+ *   1. rho = sum_i f_i, rho u = sum_i f_i c_i + F/2                       (Eq. macroscopic)
+ *   2. the pre-collision central moments k4..k8                           (Eq. pre_collision)
+ *   3. the 19 nonzero post-collision central moments, second-order moments relaxed at
+ *      omega = 1/(3 nu + 1/2), every other moment at rate 1               (Eq. eq:relaxationMatrix,
+ *                                                           Eq. post_collision_central_moments_forcing)
+ *   4. f* = (T^T)^-1 k*                                                   (Eq. system)
+ *   5. f_i(x + c_i, t + 1) = f*_i(x, t)                                   (Eq. streaming)
+ * on the D3Q27 lattice of Sec. II, in lattice units (c_s^2 = 1/3).
+ *
+ * Conventions shared by every call
+ *   - Grid: nx * ny * nz nodes; node n = x + nx*(y + ny*z) (x fastest).  Fields are arrays of
+ *     N = nx*ny*nz floats in that order; populations are 27*N floats, population i of node n
+ *     at [i*N + n], directions ordered as in Sec. II.
+ *   - Boundaries: periodic in x and z; periodic in y unless walls_y, which places halfway
+ *     bounce-back walls at y = -1/2 and y = ny - 1/2.  A mask marks solid nodes; links into
+ *     a solid node bounce back halfway: f_opp(i)(x, t+1) = f*_i(x, t).  Solid nodes are never
+ *     collided and are excluded from every diagnostic.
+ *   - Force F is a force density (the forcing term carries no rho prefactor).
+ *   - Pointers: arrays passed in may live in host or device memory (detected per call).  The
+ *     caller owns them; the library copies what it keeps and never frees them.
+ *   - Streams: every call enqueues its work on desc.stream (NULL = the legacy default stream).
+ *     lbm_step only enqueues; lbm_macroscopic, lbm_get_populations, lbm_stats and
+ *     lbm_synchronize wait for the stream.
+ *   - Errors: no call throws or aborts.  Each returns an lbm_status; lbm_last_error() gives a
+ *     message for the context (or, with NULL, for the last failed lbm_create on this thread).
+ *     A context whose call returned LBM_ERR_CUDA should be destroyed.
+ *   - Storage: populations are stored as deviations g_i = f_i - w_i rho0 in FP32, FP16 or
+ *     BF16 (round to nearest even); all collision arithmetic is FP32.
+ */
+#ifndef CMLBM_H
+#define CMLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,         /* invalid argument (sizes, pointers, kinds)                        */
+    LBM_ERR_CUDA = 2,        /* a CUDA call failed; the message names it                         */
+    LBM_ERR_OOM = 3,         /* device allocation failed                                         */
+    LBM_ERR_DIVERGED = 4,    /* some node reached rho <= 0, |u| >= 1 or NaN since the last check */
+    LBM_ERR_TIMEOUT = 5,     /* a bounded device wait gave up                                    */
+    LBM_ERR_STATE = 6,       /* call not valid in the context's current state                    */
+    LBM_ERR_UNSUPPORTED = 7  /* combination not supported (e.g. Shan-Chen with walls or masks)    */
+} lbm_status;
+
+typedef enum {
+    LBM_FP32 = 0,     /* 4 B per population */
+    LBM_FP16_DEV = 1, /* 2 B per population, IEEE half deviation */
+    LBM_BF16_DEV = 2  /* 2 B per population, bfloat16 deviation  */
+} lbm_storage;
+
+typedef enum {
+    LBM_FORCE_NONE = 0,       /* F = 0                                                            */
+    LBM_FORCE_UNIFORM = 1,    /* F = (params[0], params[1], params[2]) on every node              */
+    LBM_FORCE_KOLMOGOROV = 2, /* F_x = params[0] * sin(2 pi y / ny), F_y = F_z = 0               */
+    LBM_FORCE_FIELD = 3,      /* F from the fx, fy, fz arrays (N floats each, copied)             */
+    LBM_FORCE_SHAN_CHEN = 4   /* F = -G psi(x) sum_i w_i c_i psi(x + c_i), psi = 1 - exp(-rho),
+                                 G = params[0]; rho is the density at the current time step
+                                 (Sec. III, static droplet).  Periodic domains only.             */
+} lbm_force_kind;
+
+typedef struct {
+    int nx, ny, nz;        /* grid size, each >= 1; N = nx*ny*nz < 2^31                          */
+    double nu;             /* kinematic viscosity > 0; omega = 1/(3 nu + 1/2) (Sec. II)          */
+    double rho0;           /* reference density (> 0); initial state rho = rho0, u = 0 (Sec. III) */
+    int walls_y;           /* 1: halfway bounce-back walls at y = -1/2 and y = ny - 1/2           */
+    const uint8_t* mask;   /* NULL, or N bytes (host or device), nonzero = solid node             */
+    int storage;           /* lbm_storage                                                         */
+    void* stream;          /* cudaStream_t to run on; NULL = legacy default stream                */
+    void* store;           /* NULL: the library allocates the population store.  Otherwise a
+                              device buffer of lbm_store_bytes(desc) bytes, 256-byte aligned,
+                              owned by the caller and kept alive until lbm_destroy.               */
+} lbm_desc;
+
+/* Bytes of the population store for desc (27 * N * element size); 0 on invalid sizes. */
+LBM_API size_t lbm_store_bytes(const lbm_desc* desc);
+
+/* Creates a solver on the current CUDA device, initialised to rho = rho0, u = 0, F = 0
+ * (Sec. III: the density starts at rho0 with the fluid at rest).  On failure *out = NULL. */
+LBM_API lbm_status lbm_create(const lbm_desc* desc, lbm_ctx** out);
+
+/* Selects the force source (lbm_force_kind).  params: see the kind; may be NULL for NONE and
+ * FIELD.  fx, fy, fz: used by FIELD only (host or device, N floats each, copied). */
+LBM_API lbm_status lbm_set_force(lbm_ctx* ctx, int kind, const double* params, const float* fx, const float* fy,
+                         const float* fz);
+
+/* Sets f = f^eq(rho, u), the complete (sixth-order Hermite) equilibrium of Eq. eq:truncation,
+ * on every fluid node (rest state on solid nodes).  Arrays: N floats each, host or device.
+ * Resets the step counter to 0. */
+LBM_API lbm_status lbm_set_state(lbm_ctx* ctx, const float* rho, const float* ux, const float* uy, const float* uz);
+
+/* Sets the populations from g (27*N floats, deviations f_i - w_i rho0, host or device) and
+ * resets the step counter to 0. */
+LBM_API lbm_status lbm_set_populations(lbm_ctx* ctx, const float* g);
+
+/* Copies the populations at the current time into g (27*N floats, deviations
+ * f_i - w_i rho0, host or device), decoded from the stored precision.  Waits for the stream. */
+LBM_API lbm_status lbm_get_populations(lbm_ctx* ctx, float* g);
+
+/* Enqueues nsteps >= 0 time steps.  Returns LBM_ERR_DIVERGED if an earlier step (seen at the
+ * last synchronising call) left the physical range. */
+LBM_API lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
+
+/* Enqueues nsteps steps of free streaming: the collision is replaced by f* = f while the AA
+ * addressing, periodic wrap and halfway bounce-back are those of lbm_step.  FP32 storage only
+ * (LBM_ERR_UNSUPPORTED otherwise).  Populations move bit for bit, so a labelled state checks
+ * the streaming indices exactly. */
+LBM_API lbm_status lbm_stream_only(lbm_ctx* ctx, int nsteps);
+
+/* Writes rho and u (u includes F/2, Eq. macroscopic) at the current time.  Any output may be
+ * NULL; each is N floats, host or device.  Solid nodes get rho0 and 0.  Waits for the stream;
+ * returns LBM_ERR_DIVERGED when a step since the last check flagged a node. */
+LBM_API lbm_status lbm_macroscopic(lbm_ctx* ctx, float* rho, float* ux, float* uy, float* uz);
+
+#define LBM_STATS_LEN 10
+/* FP64 diagnostics over fluid nodes at the current time (host array of LBM_STATS_LEN):
+ *   [0] mass sum rho   [1..3] momentum sum rho u   [4] residual |u - u_prev|_2 / |u|_2, u_prev
+ *   being u at the previous lbm_stats call (1.0 on the first call)   [5] kinetic energy,
+ *   mean of |u|^2/2   [6] enstrophy, mean of |curl u|^2/2 (second-order central differences,
+ *   u = 0 behind walls and on solid nodes)   [7] max |u|   [8] fluid node count   [9] step.
+ * Deterministic: fixed reduction order.  Waits for the stream. */
+LBM_API lbm_status lbm_stats(lbm_ctx* ctx, double* out);
+
+/* Waits for the stream; LBM_ERR_DIVERGED if a step since the last check flagged a node. */
+LBM_API lbm_status lbm_synchronize(lbm_ctx* ctx);
+
+/* Kernel timing hook for benchmarks: while enabled, lbm_step records a CUDA event pair on the
+ * context's stream around every stream-collide launch and every psi launch.  It changes no
+ * result; the cost is two event records per launch. */
+LBM_API lbm_status lbm_profile(lbm_ctx* ctx, int enable);
+
+#define LBM_PROFILE_LEN 4
+/* Waits for the stream, then returns and clears the totals gathered since the last read
+ * (host array of LBM_PROFILE_LEN): [0] stream-collide kernel time in ms, [1] its launches,
+ * [2] psi kernel time in ms, [3] its launches. */
+LBM_API lbm_status lbm_profile_read(lbm_ctx* ctx, double* out);
+
+/* Time steps taken since creation or the last lbm_set_state / lbm_set_populations. */
+LBM_API long long lbm_time(const lbm_ctx* ctx);
+
+/* Message of the last error of ctx (NULL ctx: of the last lbm_create on this thread). */
+LBM_API const char* lbm_last_error(const lbm_ctx* ctx);
+LBM_API const char* lbm_status_string(int status);
+
+/* Frees everything the library allocated for ctx.  NULL is ignored.  Waits for the stream. */
+LBM_API void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CMLBM_H */

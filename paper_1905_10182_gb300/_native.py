@@ -1,0 +1,112 @@
+"""ctypes binding of libcmlbm.so (include/cmlbm.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA kernels behind the C ABI; this module only turns
+numpy arrays and torch tensors into pointers.  If the library cannot be built or loaded the
+import fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import buildlib as _build
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_STATE, \
+    LBM_ERR_UNSUPPORTED = range(8)
+LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2
+LBM_FORCE_NONE, LBM_FORCE_UNIFORM, LBM_FORCE_KOLMOGOROV, LBM_FORCE_FIELD, LBM_FORCE_SHAN_CHEN = range(5)
+LBM_STATS_LEN = 10
+LBM_PROFILE_LEN = 4
+HEADER = os.path.join(_build.ROOT, "include", "cmlbm.h")
+
+
+class LbmDesc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("nu", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("walls_y", ctypes.c_int),
+        ("mask", ctypes.c_void_p),
+        ("storage", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+        ("store", ctypes.c_void_p),
+    ]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def declared_symbols(header: str = HEADER):
+    """Names of the entry points declared in include/cmlbm.h."""
+    txt = open(header).read()
+    return sorted(set(re.findall(r"^LBM_API\s+[\w\s\*]+?\b(lbm_\w+)\s*\(", txt, flags=re.M)))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        st = ctypes.c_int
+        L.lbm_store_bytes.argtypes = [ctypes.POINTER(LbmDesc)]
+        L.lbm_store_bytes.restype = ctypes.c_size_t
+        L.lbm_create.argtypes = [ctypes.POINTER(LbmDesc), ctypes.POINTER(_P)]
+        L.lbm_create.restype = st
+        L.lbm_set_force.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P, _P, _P]
+        L.lbm_set_force.restype = st
+        L.lbm_set_state.argtypes = [_P, _P, _P, _P, _P]
+        L.lbm_set_state.restype = st
+        L.lbm_set_populations.argtypes = [_P, _P]
+        L.lbm_set_populations.restype = st
+        L.lbm_get_populations.argtypes = [_P, _P]
+        L.lbm_get_populations.restype = st
+        L.lbm_step.argtypes = [_P, ctypes.c_int]
+        L.lbm_step.restype = st
+        L.lbm_stream_only.argtypes = [_P, ctypes.c_int]
+        L.lbm_stream_only.restype = st
+        L.lbm_macroscopic.argtypes = [_P, _P, _P, _P, _P]
+        L.lbm_macroscopic.restype = st
+        L.lbm_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_double)]
+        L.lbm_stats.restype = st
+        L.lbm_synchronize.argtypes = [_P]
+        L.lbm_synchronize.restype = st
+        L.lbm_profile.argtypes = [_P, ctypes.c_int]
+        L.lbm_profile.restype = st
+        L.lbm_profile_read.argtypes = [_P, ctypes.POINTER(ctypes.c_double)]
+        L.lbm_profile_read.restype = st
+        L.lbm_time.argtypes = [_P]
+        L.lbm_time.restype = ctypes.c_longlong
+        L.lbm_last_error.argtypes = [_P]
+        L.lbm_last_error.restype = ctypes.c_char_p
+        L.lbm_status_string.argtypes = [ctypes.c_int]
+        L.lbm_status_string.restype = ctypes.c_char_p
+        L.lbm_destroy.argtypes = [_P]
+        L.lbm_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def status_name(status: int) -> str:
+    return lib().lbm_status_string(int(status)).decode()
+
+
+def ptr(a):
+    """Data pointer of a numpy array or torch tensor (must be contiguous float32/uint8), or None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")

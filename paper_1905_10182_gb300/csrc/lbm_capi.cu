@@ -1,0 +1,580 @@
+// C ABI of the solver (declared in include/cmlbm.h): context management, host/device argument
+// handling and kernel launch order.  All arithmetic runs in the kernels.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cmlbm.h"
+#include "lbm_device.cuh"
+#include "lbm_launch.h"
+
+using namespace cmlbm;
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, nz = 0;
+    long long N = 0;
+    double nu = 0, omega = 0, rho0 = 1;
+    int walls_y = 0;
+    int storage = LBM_FP32;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    void* f = nullptr;  // population store
+    bool own_f = false;
+    uint32_t* links = nullptr;  // per-node link word (null: periodic, no mask, no walls)
+
+    int force_kind = LBM_FORCE_NONE;
+    float F[3] = {0, 0, 0};
+    float G = 0;
+    float* kolm = nullptr;  // ny entries
+    float* field = nullptr; // 3N
+    float* psi = nullptr;   // N
+
+    float* macro = nullptr;  // 4N: rho, ux, uy, uz
+    float* uprev = nullptr;  // 3N
+    bool have_uprev = false;
+    double* partials = nullptr;
+    int nblocks = 0;
+    double* stats_dev = nullptr;
+    double* stats_host = nullptr;   // pinned
+    unsigned int* flag_dev = nullptr;
+    unsigned int* flag_host = nullptr;  // pinned
+
+    bool profile = false;
+    std::vector<cudaEvent_t> events;  // pool, reused after each read
+    std::vector<int> event_kind;      // per recorded pair: 0 stream-collide, 1 psi
+    size_t events_used = 0;           // events recorded since the last read (pairs * 2)
+
+    long long t = 0;
+    int parity = 0;  // 0: store in natural order; 1: after an even step
+    bool diverged = false;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+lbm_status fail(lbm_ctx* c, lbm_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+}
+
+#define CK(ctx, call, what)                                      \
+    do {                                                         \
+        cudaError_t _e = (call);                                 \
+        if (_e != cudaSuccess) return cuda_fail((ctx), _e, what); \
+    } while (0)
+
+size_t elem_size(int storage) { return storage == LBM_FP32 ? 4 : 2; }
+
+bool valid_dims(const lbm_desc* d) {
+    if (!d || d->nx < 1 || d->ny < 1 || d->nz < 1) return false;
+    const long long N = (long long)d->nx * d->ny * d->nz;
+    return N < (1LL << 31);
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+KParams make_params(const lbm_ctx* c) {
+    KParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.N = c->N;
+    p.nx = c->nx;
+    p.ny = c->ny;
+    p.nz = c->nz;
+    p.omega = (float)c->omega;
+    p.rho0 = (float)c->rho0;
+    p.F[0] = c->F[0];
+    p.F[1] = c->F[1];
+    p.F[2] = c->F[2];
+    p.G = c->G;
+    p.kolm = c->kolm;
+    if (c->field) {
+        p.fx = c->field;
+        p.fy = c->field + c->N;
+        p.fz = c->field + 2 * c->N;
+    }
+    p.psi = c->psi;
+    p.links = c->links;
+    p.flag = c->flag_dev;
+    return p;
+}
+
+int kernel_force_kind(const lbm_ctx* c) {
+    switch (c->force_kind) {
+    case LBM_FORCE_KOLMOGOROV: return FK_KOLMOGOROV;
+    case LBM_FORCE_FIELD: return FK_FIELD;
+    case LBM_FORCE_SHAN_CHEN: return FK_SHAN_CHEN;
+    default: return FK_CONST;
+    }
+}
+
+// storage-type dispatch
+#define DISPATCH(c, FN, ...)                                                                  \
+    ((c)->storage == LBM_FP32      ? FN<float>(__VA_ARGS__)                                   \
+     : (c)->storage == LBM_FP16_DEV ? FN<__half>(__VA_ARGS__)                                 \
+                                    : FN<__nv_bfloat16>(__VA_ARGS__))
+
+// Copies a caller array of `bytes` to device memory `dst` (host or device source).
+cudaError_t copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    return cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+}
+cudaError_t copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    return cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+}
+
+// Kolmogorov force table F0 sin(2 pi y / ny), evaluated in FP64 and rounded once.
+__global__ void k_kolmogorov_table(float* tab, int ny, double F0) {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y < ny) tab[y] = (float)(F0 * sinpi(2.0 * (double)y / (double)ny));
+}
+
+// Link words: bit i set when the source x - c_i of direction i lies behind a y wall or on a
+// solid node; SOLID_BIT when the node itself is solid.
+__global__ void k_build_links(uint32_t* links, const uint8_t* mask, int nx, int ny, int nz, int walls_y) {
+    const long long N = (long long)nx * ny * nz;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+        uint32_t w = 0;
+        if (mask && mask[n]) w |= SOLID_BIT;
+        for (int i = 0; i < 27; ++i) {
+            const int sx = x - dir_x(i), sy = y - dir_y(i), sz = z - dir_z(i);
+            bool blocked = false;
+            if (walls_y && (sy < 0 || sy >= ny)) blocked = true;
+            if (!blocked && mask) {
+                const int wx = (sx + nx) % nx, wy = (sy + ny) % ny, wz = (sz + nz) % nz;
+                if (mask[(long long)wx + (long long)nx * ((long long)wy + (long long)ny * wz)]) blocked = true;
+            }
+            if (blocked) w |= 1u << i;
+        }
+        links[n] = w;
+    }
+}
+
+lbm_status check_flag(lbm_ctx* c) {
+    // requires the stream to be idle
+    if (*c->flag_host) c->diverged = true;
+    if (c->diverged) return fail(c, LBM_ERR_DIVERGED, "a node reached rho <= 0, |u| >= 1 or NaN");
+    return LBM_OK;
+}
+
+lbm_status sync_and_check(lbm_ctx* c) {
+    CK(c, cudaMemcpyAsync(c->flag_host, c->flag_dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream),
+       "flag copy");
+    CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return check_flag(c);
+}
+
+lbm_status ensure_macro(lbm_ctx* c) {
+    if (!c->macro) CK(c, cudaMalloc(&c->macro, sizeof(float) * 4 * c->N), "cudaMalloc(macroscopic)");
+    return LBM_OK;
+}
+
+// psi of the current state (Shan-Chen only)
+lbm_status refresh_psi(lbm_ctx* c, const KParams& p) {
+    if (c->force_kind != LBM_FORCE_SHAN_CHEN) return LBM_OK;
+    CK(c, DISPATCH(c, launch_psi, p, c->f, c->psi, c->parity, c->stream), "psi kernel");
+    return LBM_OK;
+}
+
+lbm_status run_macro(lbm_ctx* c) {
+    lbm_status st = ensure_macro(c);
+    if (st) return st;
+    KParams p = make_params(c);
+    st = refresh_psi(c, p);
+    if (st) return st;
+    float* m = c->macro;
+    CK(c, DISPATCH(c, launch_macroscopic, p, c->f, c->parity, kernel_force_kind(c), m, m + c->N, m + 2 * c->N, m + 3 * c->N,
+                   c->stream),
+       "macroscopic kernel");
+    return LBM_OK;
+}
+
+// Records one event of a timing pair when profiling is on.
+lbm_status profile_mark(lbm_ctx* c, int kind) {
+    if (!c->profile) return LBM_OK;
+    if (c->events_used == c->events.size()) {
+        cudaEvent_t e;
+        CK(c, cudaEventCreate(&e), "cudaEventCreate");
+        c->events.push_back(e);
+    }
+    if (c->events_used % 2 == 0) c->event_kind.push_back(kind);
+    CK(c, cudaEventRecord(c->events[c->events_used], c->stream), "cudaEventRecord");
+    ++c->events_used;
+    return LBM_OK;
+}
+
+lbm_status do_steps(lbm_ctx* c, int nsteps, bool trace) {
+    KParams p = make_params(c);
+    const int fk = kernel_force_kind(c);
+    lbm_status st;
+    for (int s = 0; s < nsteps; ++s) {
+        if (!trace && c->force_kind == LBM_FORCE_SHAN_CHEN) {
+            if ((st = profile_mark(c, 1))) return st;
+            CK(c, DISPATCH(c, launch_psi, p, c->f, c->psi, c->parity, c->stream), "psi kernel");
+            if ((st = profile_mark(c, 1))) return st;
+        }
+        if ((st = profile_mark(c, 0))) return st;
+        CK(c, DISPATCH(c, launch_step, p, c->f, c->parity, fk, trace ? 1 : 0, c->stream), "stream-collide kernel");
+        if ((st = profile_mark(c, 0))) return st;
+        c->parity ^= 1;
+        ++c->t;
+    }
+    return LBM_OK;
+}
+
+void free_all(lbm_ctx* c) {
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    c->events.clear();
+    if (c->own_f && c->f) cudaFree(c->f);
+    cudaFree(c->links);
+    cudaFree(c->kolm);
+    cudaFree(c->field);
+    cudaFree(c->psi);
+    cudaFree(c->macro);
+    cudaFree(c->uprev);
+    cudaFree(c->partials);
+    cudaFree(c->stats_dev);
+    cudaFree(c->flag_dev);
+    if (c->stats_host) cudaFreeHost(c->stats_host);
+    if (c->flag_host) cudaFreeHost(c->flag_host);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_store_bytes(const lbm_desc* d) {
+    if (!valid_dims(d) || d->storage < LBM_FP32 || d->storage > LBM_BF16_DEV) return 0;
+    return (size_t)27 * (size_t)d->nx * (size_t)d->ny * (size_t)d->nz * elem_size(d->storage);
+}
+
+lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!valid_dims(d)) return fail(nullptr, LBM_ERR_ARG, "grid sizes must be >= 1 with nx*ny*nz < 2^31");
+    if (!(d->nu > 0.0) || !std::isfinite(d->nu)) return fail(nullptr, LBM_ERR_ARG, "nu must be > 0");
+    if (!(d->rho0 > 0.0) || !std::isfinite(d->rho0)) return fail(nullptr, LBM_ERR_ARG, "rho0 must be > 0");
+    if (d->storage < LBM_FP32 || d->storage > LBM_BF16_DEV) return fail(nullptr, LBM_ERR_ARG, "unknown storage");
+    if (d->store && (reinterpret_cast<uintptr_t>(d->store) % 256) != 0)
+        return fail(nullptr, LBM_ERR_ARG, "store must be 256-byte aligned");
+
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    c->nx = d->nx;
+    c->ny = d->ny;
+    c->nz = d->nz;
+    c->N = (long long)d->nx * d->ny * d->nz;
+    c->nu = d->nu;
+    c->omega = 1.0 / (3.0 * d->nu + 0.5);  // omega = (nu / c_s^2 + 1/2)^-1, Sec. II
+    c->rho0 = d->rho0;
+    c->walls_y = d->walls_y ? 1 : 0;
+    c->storage = d->storage;
+    c->stream = static_cast<cudaStream_t>(d->stream);
+
+    auto bail = [&](lbm_status st) {
+        g_create_error = c->err;
+        free_all(c);
+        delete c;
+        return st;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaGetDevice"));
+
+    const size_t bytes = lbm_store_bytes(d);
+    if (d->store) {
+        if (!is_device_ptr(d->store)) return bail(fail(c, LBM_ERR_ARG, "store is not device memory"));
+        c->f = d->store;
+    } else {
+        e = cudaMalloc(&c->f, bytes);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(populations)"));
+        c->own_f = true;
+    }
+    if ((e = cudaMalloc(&c->flag_dev, sizeof(unsigned int))) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(flag)"));
+    if ((e = cudaMallocHost(&c->flag_host, sizeof(unsigned int))) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
+    *c->flag_host = 0;
+    if ((e = cudaMemsetAsync(c->flag_dev, 0, sizeof(unsigned int), c->stream)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "cudaMemset(flag)"));
+
+    if (d->mask || d->walls_y) {
+        if ((e = cudaMalloc(&c->links, sizeof(uint32_t) * c->N)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(links)"));
+        uint8_t* dmask = nullptr;
+        if (d->mask) {
+            if ((e = cudaMalloc(&dmask, c->N)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(mask)"));
+            e = copy_in(dmask, d->mask, c->N, c->stream);
+            if (e != cudaSuccess) {
+                cudaFree(dmask);
+                return bail(cuda_fail(c, e, "mask copy"));
+            }
+        }
+        k_build_links<<<152 * 8, 256, 0, c->stream>>>(c->links, dmask, c->nx, c->ny, c->nz, c->walls_y);
+        e = cudaGetLastError();
+        cudaError_t e2 = cudaStreamSynchronize(c->stream);
+        cudaFree(dmask);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "link build"));
+    }
+    // rest state: all deviations zero (rho = rho0, u = 0; Sec. III)
+    if ((e = cudaMemsetAsync(c->f, 0, bytes, c->stream)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemset(populations)"));
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(cuda_fail(c, e, "init sync"));
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_force(lbm_ctx* c, int kind, const double* params, const float* fx, const float* fy, const float* fz) {
+    if (!c) return LBM_ERR_ARG;
+    switch (kind) {
+    case LBM_FORCE_NONE:
+        c->F[0] = c->F[1] = c->F[2] = 0.0f;
+        break;
+    case LBM_FORCE_UNIFORM:
+        if (!params) return fail(c, LBM_ERR_ARG, "UNIFORM needs params[0..2]");
+        c->F[0] = (float)params[0];
+        c->F[1] = (float)params[1];
+        c->F[2] = (float)params[2];
+        break;
+    case LBM_FORCE_KOLMOGOROV: {
+        if (!params) return fail(c, LBM_ERR_ARG, "KOLMOGOROV needs params[0] = F0");
+        if (!c->kolm) CK(c, cudaMalloc(&c->kolm, sizeof(float) * c->ny), "cudaMalloc(kolmogorov)");
+        k_kolmogorov_table<<<(c->ny + 127) / 128, 128, 0, c->stream>>>(c->kolm, c->ny, params[0]);
+        CK(c, cudaGetLastError(), "kolmogorov table");
+        break;
+    }
+    case LBM_FORCE_FIELD: {
+        if (!fx || !fy || !fz) return fail(c, LBM_ERR_ARG, "FIELD needs fx, fy, fz");
+        if (!c->field) CK(c, cudaMalloc(&c->field, sizeof(float) * 3 * c->N), "cudaMalloc(force field)");
+        const size_t b = sizeof(float) * c->N;
+        CK(c, copy_in(c->field, fx, b, c->stream), "force copy");
+        CK(c, copy_in(c->field + c->N, fy, b, c->stream), "force copy");
+        CK(c, copy_in(c->field + 2 * c->N, fz, b, c->stream), "force copy");
+        CK(c, cudaStreamSynchronize(c->stream), "force sync");
+        break;
+    }
+    case LBM_FORCE_SHAN_CHEN:
+        if (!params) return fail(c, LBM_ERR_ARG, "SHAN_CHEN needs params[0] = G");
+        if (c->walls_y || c->links) return fail(c, LBM_ERR_UNSUPPORTED, "Shan-Chen force needs a fully periodic domain");
+        c->G = (float)params[0];
+        if (!c->psi) CK(c, cudaMalloc(&c->psi, sizeof(float) * c->N), "cudaMalloc(psi)");
+        break;
+    default:
+        return fail(c, LBM_ERR_ARG, "unknown force kind");
+    }
+    c->force_kind = kind;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx* c, const float* rho, const float* ux, const float* uy, const float* uz) {
+    if (!c) return LBM_ERR_ARG;
+    if (!rho || !ux || !uy || !uz) return fail(c, LBM_ERR_ARG, "rho, ux, uy, uz are required");
+    lbm_status st = ensure_macro(c);
+    if (st) return st;
+    const size_t b = sizeof(float) * c->N;
+    float* m = c->macro;
+    CK(c, copy_in(m, rho, b, c->stream), "state copy");
+    CK(c, copy_in(m + c->N, ux, b, c->stream), "state copy");
+    CK(c, copy_in(m + 2 * c->N, uy, b, c->stream), "state copy");
+    CK(c, copy_in(m + 3 * c->N, uz, b, c->stream), "state copy");
+    KParams p = make_params(c);
+    CK(c, DISPATCH(c, launch_init_equilibrium, p, c->f, m, m + c->N, m + 2 * c->N, m + 3 * c->N, c->stream), "init kernel");
+    CK(c, cudaStreamSynchronize(c->stream), "init sync");
+    c->parity = 0;
+    c->t = 0;
+    c->have_uprev = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* c, const float* g) {
+    if (!c) return LBM_ERR_ARG;
+    if (!g) return fail(c, LBM_ERR_ARG, "g is NULL");
+    const float* src = g;
+    float* tmp = nullptr;
+    if (!is_device_ptr(g)) {
+        CK(c, cudaMalloc(&tmp, sizeof(float) * 27 * c->N), "cudaMalloc(staging)");
+        cudaError_t e = cudaMemcpyAsync(tmp, g, sizeof(float) * 27 * c->N, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_fail(c, e, "population copy");
+        }
+        src = tmp;
+    }
+    KParams p = make_params(c);
+    cudaError_t e = DISPATCH(c, launch_set_populations, p, c->f, src, c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set kernel");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "set sync");
+    c->parity = 0;
+    c->t = 0;
+    c->have_uprev = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, float* g) {
+    if (!c) return LBM_ERR_ARG;
+    if (!g) return fail(c, LBM_ERR_ARG, "g is NULL");
+    float* dst = g;
+    float* tmp = nullptr;
+    const bool dev = is_device_ptr(g);
+    if (!dev) {
+        CK(c, cudaMalloc(&tmp, sizeof(float) * 27 * c->N), "cudaMalloc(staging)");
+        dst = tmp;
+    }
+    KParams p = make_params(c);
+    cudaError_t e = DISPATCH(c, launch_get_populations, p, c->f, c->parity, dst, c->stream);
+    if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(g, tmp, sizeof(float) * 27 * c->N, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get populations");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "get sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int nsteps) {
+    if (!c) return LBM_ERR_ARG;
+    if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps < 0");
+    if (c->diverged) return fail(c, LBM_ERR_DIVERGED, "the solution diverged earlier");
+    return do_steps(c, nsteps, false);
+}
+
+lbm_status lbm_stream_only(lbm_ctx* c, int nsteps) {
+    if (!c) return LBM_ERR_ARG;
+    if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps < 0");
+    if (c->storage != LBM_FP32) return fail(c, LBM_ERR_UNSUPPORTED, "free streaming needs FP32 storage");
+    return do_steps(c, nsteps, true);
+}
+
+lbm_status lbm_macroscopic(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz) {
+    if (!c) return LBM_ERR_ARG;
+    lbm_status st = run_macro(c);
+    if (st) return st;
+    float* outs[4] = {rho, ux, uy, uz};
+    for (int k = 0; k < 4; ++k)
+        if (outs[k]) CK(c, copy_out(outs[k], c->macro + k * c->N, sizeof(float) * c->N, c->stream), "macroscopic copy");
+    return sync_and_check(c);
+}
+
+lbm_status lbm_stats(lbm_ctx* c, double* out) {
+    if (!c) return LBM_ERR_ARG;
+    if (!out) return fail(c, LBM_ERR_ARG, "out is NULL");
+    lbm_status st = run_macro(c);
+    if (st) return st;
+    if (!c->uprev) CK(c, cudaMalloc(&c->uprev, sizeof(float) * 3 * c->N), "cudaMalloc(u_prev)");
+    if (!c->partials) {
+        c->nblocks = reduce_blocks(c->N);
+        CK(c, cudaMalloc(&c->partials, sizeof(double) * REDUCE_FIELDS * c->nblocks), "cudaMalloc(partials)");
+        CK(c, cudaMalloc(&c->stats_dev, sizeof(double) * REDUCE_FIELDS), "cudaMalloc(stats)");
+        CK(c, cudaMallocHost(&c->stats_host, sizeof(double) * REDUCE_FIELDS), "cudaMallocHost(stats)");
+    }
+    ReduceArgs a;
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.nz = c->nz;
+    a.walls_y = c->walls_y;
+    a.links = c->links;
+    a.rho = c->macro;
+    a.ux = c->macro + c->N;
+    a.uy = c->macro + 2 * c->N;
+    a.uz = c->macro + 3 * c->N;
+    a.uprev = c->have_uprev ? c->uprev : nullptr;
+    CK(c, launch_reduce(a, c->partials, c->nblocks, c->stats_dev, c->stream), "reduce kernels");
+    CK(c, cudaMemcpyAsync(c->stats_host, c->stats_dev, sizeof(double) * REDUCE_FIELDS, cudaMemcpyDeviceToHost, c->stream),
+       "stats copy");
+    CK(c, cudaMemcpyAsync(c->uprev, c->macro + c->N, sizeof(float) * 3 * c->N, cudaMemcpyDeviceToDevice, c->stream),
+       "u_prev copy");
+    st = sync_and_check(c);
+    c->have_uprev = true;
+    const double* s = c->stats_host;
+    const double cnt = s[8];
+    out[0] = s[0];
+    out[1] = s[1];
+    out[2] = s[2];
+    out[3] = s[3];
+    out[4] = s[5] > 0.0 ? std::sqrt(s[4] / s[5]) : 0.0;
+    out[5] = cnt > 0 ? 0.5 * s[5] / cnt : 0.0;
+    out[6] = cnt > 0 ? s[6] / cnt : 0.0;
+    out[7] = std::sqrt(s[7]);
+    out[8] = cnt;
+    out[9] = (double)c->t;
+    return st;
+}
+
+lbm_status lbm_synchronize(lbm_ctx* c) {
+    if (!c) return LBM_ERR_ARG;
+    return sync_and_check(c);
+}
+
+lbm_status lbm_profile(lbm_ctx* c, int enable) {
+    if (!c) return LBM_ERR_ARG;
+    c->profile = enable != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_ctx* c, double* out) {
+    if (!c) return LBM_ERR_ARG;
+    if (!out) return fail(c, LBM_ERR_ARG, "out is NULL");
+    CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    double ms[2] = {0, 0}, n[2] = {0, 0};
+    for (size_t k = 0; k + 1 < c->events_used; k += 2) {
+        float t = 0;
+        CK(c, cudaEventElapsedTime(&t, c->events[k], c->events[k + 1]), "cudaEventElapsedTime");
+        const int kind = c->event_kind[k / 2];
+        ms[kind] += t;
+        n[kind] += 1;
+    }
+    c->events_used = 0;
+    c->event_kind.clear();
+    out[0] = ms[0];
+    out[1] = n[0];
+    out[2] = ms[1];
+    out[3] = n[1];
+    return LBM_OK;
+}
+
+long long lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+const char* lbm_status_string(int s) {
+    switch (s) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_ERR_ARG: return "LBM_ERR_ARG";
+    case LBM_ERR_CUDA: return "LBM_ERR_CUDA";
+    case LBM_ERR_OOM: return "LBM_ERR_OOM";
+    case LBM_ERR_DIVERGED: return "LBM_ERR_DIVERGED";
+    case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT";
+    case LBM_ERR_STATE: return "LBM_ERR_STATE";
+    case LBM_ERR_UNSUPPORTED: return "LBM_ERR_UNSUPPORTED";
+    default: return "unknown status";
+    }
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

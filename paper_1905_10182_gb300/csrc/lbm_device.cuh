@@ -1,0 +1,356 @@
+// Device-side building blocks of the fused D3Q27 central-moment stream-and-collide step
+// (De Rosis, Huang & Coreixas, arXiv 1905.10182, Sec. II).
+//
+// Storage: structure of arrays, population i of node n at f[i*N + n], n = x + nx*(y + ny*z),
+// one array updated in place with the AA access pattern.  What is stored is the deviation
+// g_i = f_i - w_i*rho0 from the rest state, in FP32, FP16 or BF16; all arithmetic is FP32 and
+// works on deviations throughout, so that no step subtracts two O(1) numbers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cmlbm {
+
+// ----------------------------------------------------------------------------- lattice
+// D3Q27 velocities in the order of Sec. II.
+__host__ __device__ constexpr int dir_x(int i) {
+    constexpr int t[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int dir_y(int i) {
+    constexpr int t[27] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, 1, -1, -1, 1, 1, -1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int dir_z(int i) {
+    constexpr int t[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 1, 1, 1, 1, -1, -1, -1, -1};
+    return t[i];
+}
+// index of -c_i
+__host__ __device__ constexpr int dir_opp(int i) {
+    int r = 0;
+    for (int j = 0; j < 27; ++j)
+        if (dir_x(j) == -dir_x(i) && dir_y(j) == -dir_y(i) && dir_z(j) == -dir_z(i)) r = j;
+    return r;
+}
+// D1Q3 weights (c = -1, 0, +1) and the D3Q27 weight as their product
+__host__ __device__ constexpr float w1(int c) { return c == 0 ? 2.0f / 3.0f : 1.0f / 6.0f; }
+__host__ __device__ constexpr float weight(int i) { return w1(dir_x(i)) * w1(dir_y(i)) * w1(dir_z(i)); }
+
+constexpr uint32_t SOLID_BIT = 1u << 31;  // in a link word: the node itself is solid
+
+// ----------------------------------------------------------------------------- codecs
+template <typename S>
+struct Codec;
+template <>
+struct Codec<float> {
+    static __device__ __forceinline__ float ld(const float* p) { return *p; }
+    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <>
+struct Codec<__half> {
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Codec<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ----------------------------------------------------------------------------- parameters
+enum ForceKind { FK_CONST = 0, FK_KOLMOGOROV = 1, FK_FIELD = 2, FK_SHAN_CHEN = 3 };
+
+struct KParams {
+    long long N;  // nodes
+    int nx, ny, nz;
+    float omega;  // rate of k4..k8 (Eq. eq:relaxationMatrix)
+    float rho0;
+    float F[3];            // FK_CONST force density
+    float G;               // FK_SHAN_CHEN strength
+    const float* kolm;     // FK_KOLMOGOROV: F_x(y), ny entries
+    const float* fx;       // FK_FIELD
+    const float* fy;
+    const float* fz;
+    const float* psi;      // FK_SHAN_CHEN: psi = 1 - exp(-rho) of every node
+    const uint32_t* links; // bit i: the source x - c_i of direction i is blocked; SOLID_BIT: solid node
+    unsigned int* flag;    // set to 1 when a node has rho <= 0, |u| >= 1 or a NaN
+};
+
+// Node coordinates and the offsets of its 26 neighbours with periodic wrap in x, y, z.
+struct Nbr {
+    uint32_t xo[3];  // x - 1, x, x + 1
+    uint32_t yo[3];  // row offsets of y - 1, y, y + 1
+    uint32_t zo[3];  // plane offsets of z - 1, z, z + 1
+    __device__ __forceinline__ Nbr(int x, int y, int z, const KParams& p) {
+        const uint32_t nx = p.nx, ny = p.ny, nz = p.nz;
+        xo[0] = x == 0 ? nx - 1 : x - 1;
+        xo[1] = x;
+        xo[2] = x == (int)nx - 1 ? 0 : x + 1;
+        const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == (int)ny - 1 ? 0 : y + 1;
+        yo[0] = ym * nx;
+        yo[1] = (uint32_t)y * nx;
+        yo[2] = yp * nx;
+        const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == (int)nz - 1 ? 0 : z + 1;
+        const uint32_t pl = nx * ny;
+        zo[0] = zm * pl;
+        zo[1] = (uint32_t)z * pl;
+        zo[2] = zp * pl;
+    }
+    // node index of x + (dx, dy, dz), d* in {-1, 0, 1}
+    __device__ __forceinline__ uint32_t at(int dx, int dy, int dz) const { return zo[dz + 1] + yo[dy + 1] + xo[dx + 1]; }
+    __device__ __forceinline__ uint32_t self() const { return zo[1] + yo[1] + xo[1]; }
+};
+
+// ----------------------------------------------------------------------------- AA access
+// Even step (storage in natural order): node x reads f_i from its own slot i and writes
+// f*_i into its own slot opp(i).  Odd step: f_i(x) is in slot opp(i) of x - c_i (or, when that
+// source is blocked, in slot i of x: halfway bounce-back); f*_i goes to slot i of x + c_i (or,
+// when x + c_i is blocked, to slot opp(i) of x).  Each node reads and writes the same 27
+// slots, so the update is race free in place and leaves natural order after every odd step.
+template <typename S, bool ODD, bool LINKS>
+__device__ __forceinline__ void aa_gather(const S* __restrict__ f, long long N, const Nbr& nb, uint32_t link,
+                                          float (&g)[27]) {
+    const uint32_t self = nb.self();
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        const S* p;
+        if (!ODD) {
+            p = f + (long long)i * N + self;
+        } else {
+            const bool blocked = LINKS && ((link >> i) & 1u);
+            p = blocked ? f + (long long)i * N + self
+                        : f + (long long)dir_opp(i) * N + nb.at(-dir_x(i), -dir_y(i), -dir_z(i));
+        }
+        g[i] = Codec<S>::ld(p);
+    }
+}
+
+template <typename S, bool ODD, bool LINKS>
+__device__ __forceinline__ void aa_scatter(S* __restrict__ f, long long N, const Nbr& nb, uint32_t link,
+                                           const float (&g)[27]) {
+    const uint32_t self = nb.self();
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        S* p;
+        if (!ODD) {
+            p = f + (long long)dir_opp(i) * N + self;
+        } else {
+            // x + c_i is blocked exactly when the source of direction opp(i) is
+            const bool blocked = LINKS && ((link >> dir_opp(i)) & 1u);
+            p = blocked ? f + (long long)dir_opp(i) * N + self
+                        : f + (long long)i * N + nb.at(dir_x(i), dir_y(i), dir_z(i));
+        }
+        Codec<S>::st(p, g[i]);
+    }
+}
+
+// ----------------------------------------------------------------------------- moments
+// Raw moments of the deviations, sum_i g_i cx^a cy^b cz^c for a + b + c <= 2, by three
+// D1Q3 sums (along z, then y, then x).
+struct RawMoments {
+    float m000, m100, m010, m001, m200, m020, m002, m110, m101, m011;
+};
+
+__device__ __forceinline__ RawMoments raw_moments(const float (&g)[27]) {
+    float G[3][3][3];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) G[dir_x(i) + 1][dir_y(i) + 1][dir_z(i) + 1] = g[i];
+    float S[3][3][3];  // [cx][cy][z-moment]
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float s2 = G[a][b][2] + G[a][b][0];
+            S[a][b][0] = s2 + G[a][b][1];
+            S[a][b][1] = G[a][b][2] - G[a][b][0];
+            S[a][b][2] = s2;
+        }
+    float T[3][3][3];  // [cx][y-moment][z-moment]
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float s2 = S[a][2][q] + S[a][0][q];
+            T[a][0][q] = s2 + S[a][1][q];
+            T[a][1][q] = S[a][2][q] - S[a][0][q];
+            T[a][2][q] = s2;
+        }
+    RawMoments m;
+    m.m000 = T[0][0][0] + T[1][0][0] + T[2][0][0];
+    m.m100 = T[2][0][0] - T[0][0][0];
+    m.m200 = T[2][0][0] + T[0][0][0];
+    m.m010 = T[0][1][0] + T[1][1][0] + T[2][1][0];
+    m.m001 = T[0][0][1] + T[1][0][1] + T[2][0][1];
+    m.m020 = T[0][2][0] + T[1][2][0] + T[2][2][0];
+    m.m002 = T[0][0][2] + T[1][0][2] + T[2][0][2];
+    m.m110 = T[2][1][0] - T[0][1][0];
+    m.m101 = T[2][0][1] - T[0][0][1];
+    m.m011 = T[0][1][1] + T[1][1][1] + T[2][1][1];
+    return m;
+}
+
+// ----------------------------------------------------------------------------- inverse
+// One D1Q3 inverse of the fast CM transform in deviation form.  Input: central moments
+// (m0, m1, m2) about the shift u, minus the rest-state moments r*(1, 0, 1/3); output: the three
+// populations c = -1, 0, +1 minus the rest populations r*(1/6, 2/3, 1/6).  With A = r + m0:
+//   p0 = m0 - A u^2 - 2 u m1 - m2,   p(+-1) = [A (u^2 +- u) + m1 (2u +- 1) + m2] / 2,
+// the exact D1Q3 inverse (raw moments M1 = m1 + u m0, M2 = m2 + 2u m1 + u^2 m0; f0 = M0 - M2,
+// f(+-1) = (M2 +- M1)/2) with the rest state subtracted analytically.
+__device__ __forceinline__ void d1q3_inverse_dev(float m0, float m1, float m2, float r, float u, float u2,
+                                                 float& pm, float& p0, float& pp) {
+    const float A = r + m0;
+    const float Au2 = A * u2;
+    const float Au = A * u;
+    const float t = Au2 + m2 + 2.0f * u * m1;
+    p0 = m0 - t;
+    pp = 0.5f * (t + Au + m1);
+    pm = 0.5f * (t - Au - m1);
+}
+
+// kd[a][b][c]: post-collision central moments kappa_abc (x order a, y order b, z order c)
+// minus the rest-state moments rho0 * s_a s_b s_c, s = (1, 0, 1/3).  Writes the deviations
+// of the 27 populations into g.
+__device__ __forceinline__ void inverse_fast_dev(const float (&kd)[3][3][3], float ux, float uy, float uz, float rho0,
+                                                 float (&g)[27]) {
+    constexpr float s[3] = {1.0f, 0.0f, 1.0f / 3.0f};
+    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    float H[3][3][3];  // [x order][y order][cz]
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float r = rho0 * s[a] * s[b];
+            d1q3_inverse_dev(kd[a][b][0], kd[a][b][1], kd[a][b][2], r, uz, uz2, H[a][b][0], H[a][b][1], H[a][b][2]);
+        }
+    float K[3][3][3];  // [x order][cy][cz]
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float r = rho0 * s[a] * w1(c - 1);
+            d1q3_inverse_dev(H[a][0][c], H[a][1][c], H[a][2][c], r, uy, uy2, K[a][0][c], K[a][1][c], K[a][2][c]);
+        }
+    float P[3][3][3];  // [cx][cy][cz]
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float r = rho0 * w1(b - 1) * w1(c - 1);
+            d1q3_inverse_dev(K[0][b][c], K[1][b][c], K[2][b][c], r, ux, ux2, P[0][b][c], P[1][b][c], P[2][b][c]);
+        }
+#pragma unroll
+    for (int i = 0; i < 27; ++i) g[i] = P[dir_x(i) + 1][dir_y(i) + 1][dir_z(i) + 1];
+}
+
+// ----------------------------------------------------------------------------- collision
+// The time iteration of Sec. II (steps 1-4), on deviations:
+//  1. rho = rho0 + sum g, rho u = sum g c + F/2                       (Eq. macroscopic)
+//  2. k4..k8 from the raw second moments: kappa_ab = Pi_ab - rho u_a u_b + (u_a F_b + u_b F_a)/2
+//                                                                       (Eq. pre_collision)
+//  3. the 19 nonzero post-collision CMs                 (Eq. post_collision_central_moments_forcing)
+//  4. f* = (T^T)^-1 k* through the factorised (fast) CM transform       (Eq. system)
+struct Macro {
+    float rho, ux, uy, uz;
+};
+
+__device__ __forceinline__ Macro collide_cm(float (&g)[27], float Fx, float Fy, float Fz, float omega, float rho0) {
+    const RawMoments m = raw_moments(g);
+    const float dr = m.m000;
+    const float rho = rho0 + dr;
+    const float inv = 1.0f / rho;
+    const float ux = (m.m100 + 0.5f * Fx) * inv;
+    const float uy = (m.m010 + 0.5f * Fy) * inv;
+    const float uz = (m.m001 + 0.5f * Fz) * inv;
+
+    const float k4 = m.m110 - rho * ux * uy + 0.5f * (ux * Fy + uy * Fx);
+    const float k5 = m.m101 - rho * ux * uz + 0.5f * (ux * Fz + uz * Fx);
+    const float k6 = m.m011 - rho * uy * uz + 0.5f * (uy * Fz + uz * Fy);
+    const float uFx = ux * Fx, uFy = uy * Fy, uFz = uz * Fz;
+    const float k7 = (m.m200 - m.m020) - rho * (ux * ux - uy * uy) + uFx - uFy;
+    const float k8 = (m.m200 - m.m002) - rho * (ux * ux - uz * uz) + uFx - uFz;
+
+    const float om1 = 1.0f - omega;
+    const float k4s = om1 * k4, k5s = om1 * k5, k6s = om1 * k6, k7s = om1 * k7, k8s = om1 * k8;
+
+    // kappa*_abc from k*: k7 = k200 - k020, k8 = k200 - k002, k9 = k200 + k020 + k002 = rho;
+    // k10/k13 -> k120 = k102 = Fx c_s^2/2 (and cyclic); k17..k19 -> k220 = k202 = k022 = rho c_s^4;
+    // k23..k25 -> k122 = Fx c_s^4/2 (and cyclic); k26 = k222 = rho c_s^6.  Deviations from rest.
+    const float third = 1.0f / 3.0f;
+    float kd[3][3][3];
+    kd[0][0][0] = dr;
+    kd[1][0][0] = 0.5f * Fx;
+    kd[0][1][0] = 0.5f * Fy;
+    kd[0][0][1] = 0.5f * Fz;
+    kd[1][1][0] = k4s;
+    kd[1][0][1] = k5s;
+    kd[0][1][1] = k6s;
+    kd[2][0][0] = (k7s + k8s + dr) * third;
+    kd[0][2][0] = (dr - 2.0f * k7s + k8s) * third;
+    kd[0][0][2] = (dr + k7s - 2.0f * k8s) * third;
+    kd[1][2][0] = kd[1][0][2] = Fx * (1.0f / 6.0f);
+    kd[2][1][0] = kd[0][1][2] = Fy * (1.0f / 6.0f);
+    kd[2][0][1] = kd[0][2][1] = Fz * (1.0f / 6.0f);
+    kd[1][1][1] = 0.0f;
+    kd[2][2][0] = kd[2][0][2] = kd[0][2][2] = dr * (1.0f / 9.0f);
+    kd[2][1][1] = kd[1][2][1] = kd[1][1][2] = 0.0f;
+    kd[1][2][2] = Fx * (1.0f / 18.0f);
+    kd[2][1][2] = Fy * (1.0f / 18.0f);
+    kd[2][2][1] = Fz * (1.0f / 18.0f);
+    kd[2][2][2] = dr * (1.0f / 27.0f);
+
+    inverse_fast_dev(kd, ux, uy, uz, rho0, g);
+    return Macro{rho, ux, uy, uz};
+}
+
+// Equilibrium deviations g_i = f_i^eq(rho, u) - w_i rho0: the equilibrium CMs of
+// Eq. equil_central_moments6 are rho * s_a s_b s_c, so the inverse runs on (rho - rho0) s_a s_b s_c.
+__device__ __forceinline__ void equilibrium_dev(float rho, float ux, float uy, float uz, float rho0, float (&g)[27]) {
+    constexpr float s[3] = {1.0f, 0.0f, 1.0f / 3.0f};
+    const float dr = rho - rho0;
+    float kd[3][3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) kd[a][b][c] = dr * s[a] * s[b] * s[c];
+    inverse_fast_dev(kd, ux, uy, uz, rho0, g);
+}
+
+// ----------------------------------------------------------------------------- forces
+template <int FK>
+__device__ __forceinline__ void node_force(const KParams& p, const Nbr& nb, int y, float& Fx, float& Fy, float& Fz) {
+    if (FK == FK_CONST) {
+        Fx = p.F[0];
+        Fy = p.F[1];
+        Fz = p.F[2];
+    } else if (FK == FK_KOLMOGOROV) {
+        Fx = p.kolm[y];
+        Fy = 0.0f;
+        Fz = 0.0f;
+    } else if (FK == FK_FIELD) {
+        const uint32_t n = nb.self();
+        Fx = p.fx[n];
+        Fy = p.fy[n];
+        Fz = p.fz[n];
+    } else {
+        // Shan-Chen (Sec. III, static droplet): F = -G psi(x) sum_i w_i c_i psi(x + c_i)
+        float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+        for (int i = 1; i < 27; ++i) {
+            const float v = weight(i) * p.psi[nb.at(dir_x(i), dir_y(i), dir_z(i))];
+            if (dir_x(i)) sx += dir_x(i) > 0 ? v : -v;
+            if (dir_y(i)) sy += dir_y(i) > 0 ? v : -v;
+            if (dir_z(i)) sz += dir_z(i) > 0 ? v : -v;
+        }
+        const float a = -p.G * p.psi[nb.self()];
+        Fx = a * sx;
+        Fy = a * sy;
+        Fz = a * sz;
+    }
+}
+
+}  // namespace cmlbm

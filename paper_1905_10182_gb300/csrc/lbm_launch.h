@@ -1,0 +1,46 @@
+// Host-side launch interface between the C-ABI (lbm_capi.cu) and the kernels, which are
+// instantiated once per storage type in lbm_kernels_{f32,f16,bf16}.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace cmlbm {
+
+struct KParams;
+
+template <typename S, bool ODD>
+cudaError_t launch_step_parity(const KParams& p, void* f, int fk, int trace, cudaStream_t st);
+template <typename S>
+inline cudaError_t launch_step(const KParams& p, void* f, int odd, int fk, int trace, cudaStream_t st) {
+    return odd ? launch_step_parity<S, true>(p, f, fk, trace, st) : launch_step_parity<S, false>(p, f, fk, trace, st);
+}
+template <typename S>
+cudaError_t launch_psi(const KParams& p, const void* f, float* psi, int odd, cudaStream_t st);
+template <typename S>
+cudaError_t launch_macroscopic(const KParams& p, const void* f, int odd, int fk, float* rho, float* ux, float* uy,
+                               float* uz, cudaStream_t st);
+template <typename S>
+cudaError_t launch_get_populations(const KParams& p, const void* f, int odd, float* out, cudaStream_t st);
+template <typename S>
+cudaError_t launch_set_populations(const KParams& p, void* f, const float* in, cudaStream_t st);
+template <typename S>
+cudaError_t launch_init_equilibrium(const KParams& p, void* f, const float* rho, const float* ux, const float* uy,
+                                    const float* uz, cudaStream_t st);
+
+// lbm_reduce.cu: FP64 diagnostics over the macroscopic fields
+struct ReduceArgs {
+    int nx, ny, nz;
+    int walls_y;
+    const unsigned int* links;  // may be null
+    const float* rho;
+    const float* ux;
+    const float* uy;
+    const float* uz;
+    const float* uprev;  // 3N, may be null (residual then uses 0)
+};
+constexpr int REDUCE_FIELDS = 9;   // per-block partial sums
+constexpr int REDUCE_THREADS = 256;
+int reduce_blocks(long long N);     // number of partial-sum blocks for N nodes
+cudaError_t launch_reduce(const ReduceArgs& a, double* partials, int nblocks, double* out, cudaStream_t st);
+
+}  // namespace cmlbm

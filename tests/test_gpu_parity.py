@@ -1,0 +1,288 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on the same seeded inputs.
+
+Tolerances (FP32 arithmetic on deviations):
+  one step:  |g_gpu - g_oracle| <= C * eps32 * S, eps32 = 2^-24, C = 64, where S is the largest
+             magnitude entering the deviation-form arithmetic, max(|g|, rho0 |u|, |F|);
+  n steps:   n times the one-step bound;
+  streaming indices and masks: bit-exact;
+  Kolmogorov flow at FP32 storage after 1000 steps: max |u - u_oracle| / U0 <= 1e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1905_10182_gb300 import Solver, inputs  # noqa: E402
+from paper_1905_10182_gb300._native import LbmError, LBM_ERR_DIVERGED  # noqa: E402
+
+EPS32 = 2.0 ** -24
+C_STEP = 64.0
+
+
+def full(orc, g, rho0=1.0):
+    """FP32 deviations -> FP64 full populations with the oracle's weights."""
+    return g.astype(np.float64) + rho0 * orc.weights()[:, None, None, None]
+
+
+def dev(orc, f, rho0=1.0):
+    return f - rho0 * orc.weights()[:, None, None, None]
+
+
+def scale(orc, f, og=None):
+    """Largest magnitude entering the deviation arithmetic: max(|g|, |u|, |F|) (rho0 = 1)."""
+    rho = f.sum(axis=0)
+    c = orc.velocities().astype(float)
+    mom = np.einsum("ia,izyx->azyx", c, f)
+    S = max(np.abs(dev(orc, f)).max(), np.abs(mom / rho).max())
+    if og is not None:
+        S = max(S, np.abs(og.force_field(f)).max())
+    return S
+
+
+RAGGED = (19, 13, 11)  # several 128-wide x tiles are not needed: ragged in every axis
+
+
+def _case(name, orc):
+    nx, ny, nz = RAGGED
+    g = inputs.random_deviations(nx, ny, nz, seed=1)
+    kw = dict(nu=0.07)
+    okw = dict(nu=0.07)
+    force = None
+    if name == "periodic_uniform":
+        force = ("uniform", (2e-4, -1e-4, 5e-5))
+        okw.update(force_kind=orc.FORCE_UNIFORM, force=(2e-4, -1e-4, 5e-5))
+    elif name == "kolmogorov":
+        force = ("kolmogorov", (1e-4,))
+        okw.update(force_kind=orc.FORCE_KOLMOGOROV, force=(1e-4, 0, 0))
+    elif name == "field":
+        F = inputs.random_force_field(nx, ny, nz, seed=2)
+        force = ("field", None, F[0], F[1], F[2])
+        okw.update(force_kind=orc.FORCE_FIELD, field=F.astype(np.float64))
+    elif name == "walls_mask":
+        mask = inputs.random_mask(nx, ny, nz, seed=3, fraction=0.15)
+        kw.update(walls_y=True, mask=mask)
+        okw.update(walls_y=True, mask=mask, force_kind=orc.FORCE_UNIFORM, force=(3e-4, 0, -2e-4))
+        force = ("uniform", (3e-4, 0, -2e-4))
+    elif name == "walls_only":
+        kw.update(walls_y=True)
+        okw.update(walls_y=True, force_kind=orc.FORCE_UNIFORM, force=(1e-4, 0, 0))
+        force = ("uniform", (1e-4, 0, 0))
+    elif name == "shan_chen":
+        rho = 1.0 + 0.2 * np.random.default_rng(4).random((nz, ny, nx))
+        g = inputs.random_deviations(nx, ny, nz, seed=5, density=rho)
+        kw.update(nu=0.1)
+        okw.update(nu=0.1, force_kind=orc.FORCE_SHAN_CHEN, G=-5.5)
+        force = ("shan_chen", (-5.5,))
+    return g, kw, okw, force
+
+
+CASES = ["periodic_uniform", "kolmogorov", "field", "walls_mask", "walls_only", "shan_chen"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_steps_match_oracle(orc, name):
+    """1, 2 and 3 fused steps (both AA parities) against the oracle's two-array step."""
+    g, kw, okw, force = _case(name, orc)
+    nx, ny, nz = RAGGED
+    s = Solver(nx, ny, nz, **kw)
+    if force:
+        s.set_force(*force)
+    s.set_populations(g)
+    og = orc.Grid(nx, ny, nz, collision=orc.COLL_PAPER, **okw)
+    f = full(orc, g)
+    S = scale(orc, f, og)
+    fluid = np.ones((nz, ny, nx), bool) if kw.get("mask") is None else kw["mask"] == 0
+    for n in (1, 2, 3):
+        s.step(1)
+        f = og.step(f, 1)
+        got = s.get_populations().astype(np.float64)
+        err = np.abs(got - dev(orc, f))[:, fluid].max()
+        tol = n * C_STEP * EPS32 * S
+        assert err <= tol, (name, n, err, tol)
+
+
+@pytest.mark.parametrize("walls,use_mask", [(False, False), (True, False), (False, True), (True, True)])
+def test_streaming_indices_bit_exact(orc, walls, use_mask):
+    """Free streaming of integer labels (identity collision): every label lands in exactly the slot
+    the oracle's two-array pull with halfway bounce-back puts it, for both AA parities."""
+    nx, ny, nz = RAGGED
+    mask = inputs.random_mask(nx, ny, nz, seed=6, fraction=0.2) if use_mask else None
+    lab = np.arange(27 * nx * ny * nz, dtype=np.float32).reshape(27, nz, ny, nx)
+    s = Solver(nx, ny, nz, nu=0.1, walls_y=walls, mask=mask)
+    s.set_populations(lab)
+    og = orc.Grid(nx, ny, nz, omega=1.0, collision=orc.COLL_NONE, walls_y=walls, mask=mask)
+    ref = lab.astype(np.float64)
+    for _ in range(4):
+        s.stream_only(1)
+        ref = og.step(ref, 1)
+        assert np.array_equal(s.get_populations(), ref.astype(np.float32))
+
+
+def test_equilibrium_initialisation(orc):
+    """lbm_set_state builds the complete equilibrium of Eq. eq:truncation."""
+    nx, ny, nz = RAGGED
+    rng = np.random.default_rng(7)
+    rho = rng.uniform(0.7, 1.4, (nz, ny, nx)).astype(np.float32)
+    u = rng.uniform(-0.1, 0.1, (3, nz, ny, nx)).astype(np.float32)
+    s = Solver(nx, ny, nz, nu=0.1)
+    s.set_state(rho, u[0], u[1], u[2])
+    ref = dev(orc, orc.Grid(nx, ny, nz, nu=0.1).init_equilibrium(rho.astype(np.float64), u.astype(np.float64)))
+    err = np.abs(s.get_populations() - ref).max()
+    assert err <= C_STEP * EPS32 * 1.4
+
+
+@pytest.mark.parametrize("name", ["kolmogorov", "field", "shan_chen", "walls_mask"])
+def test_macroscopic_fields(orc, name):
+    """lbm_macroscopic: rho and u including F/2 (Eq. macroscopic)."""
+    g, kw, okw, force = _case(name, orc)
+    nx, ny, nz = RAGGED
+    s = Solver(nx, ny, nz, **kw)
+    if force:
+        s.set_force(*force)
+    s.set_populations(g)
+    s.step(1)
+    og = orc.Grid(nx, ny, nz, collision=orc.COLL_PAPER, **okw)
+    f = og.step(full(orc, g), 1)
+    rho, ux, uy, uz = s.macroscopic()
+    orho, ou = og.macroscopic(f)
+    fluid = np.ones((nz, ny, nx), bool) if kw.get("mask") is None else kw["mask"] == 0
+    S = scale(orc, f, og)
+    assert np.abs(rho - orho)[fluid].max() <= 2 * C_STEP * EPS32 * 2.0
+    for a, b in zip((ux, uy, uz), ou):
+        assert np.abs(a - b)[fluid].max() <= 2 * C_STEP * EPS32 * S * 4
+
+
+def test_kolmogorov_1000_steps_fp32(orc):
+    """Kolmogorov flow 32^3, nu = 0.05, F0 = 1e-5: after 1000 steps the FP32-storage field is within
+    1e-6 U0 of the FP64 oracle (1D-reduced: the flow depends on y only, pinned in the oracle tests)."""
+    N, nu, F0, steps = 32, 0.05, 1e-5, 1000
+    s = Solver(N, N, N, nu=nu)
+    s.set_force("kolmogorov", (F0,))
+    s.step(steps)
+    rho, ux, uy, uz = s.macroscopic()
+    og = orc.Grid(1, N, 1, nu=nu, force_kind=orc.FORCE_KOLMOGOROV, force=(F0, 0, 0))
+    f = og.step(og.init_equilibrium(1.0, np.zeros((3, 1, N, 1))), steps)
+    _, ou = og.macroscopic(f)
+    k = 2 * math.pi / N
+    U0 = F0 / (nu * k * k)
+    err = max(np.abs(ux - ou[0]).max(), np.abs(uy - ou[1]).max(), np.abs(uz - ou[2]).max()) / U0
+    print(f"kolmogorov fp32 max|u - u_oracle|/U0 = {err:.3e}")
+    assert err <= 1e-6
+
+
+@pytest.mark.parametrize("storage,bound", [("fp16", 5e-3), ("bf16", 0.5)])
+def test_kolmogorov_reduced_precision_measured(orc, storage, bound):
+    """FP16/BF16 deviation storage: the measured error after 1000 steps is reported (and kept under
+    a loose sanity bound)."""
+    N, nu, F0, steps = 32, 0.05, 1e-5, 1000
+    s = Solver(N, N, N, nu=nu, storage=storage)
+    s.set_force("kolmogorov", (F0,))
+    s.step(steps)
+    _, ux, uy, uz = s.macroscopic()
+    og = orc.Grid(1, N, 1, nu=nu, force_kind=orc.FORCE_KOLMOGOROV, force=(F0, 0, 0))
+    _, ou = og.macroscopic(og.step(og.init_equilibrium(1.0, np.zeros((3, 1, N, 1))), steps))
+    U0 = F0 / (nu * (2 * math.pi / N) ** 2)
+    err = np.abs(ux - ou[0]).max() / U0
+    print(f"kolmogorov {storage} max|u - u_oracle|/U0 = {err:.3e}")
+    assert err <= bound
+
+
+def test_stats_match_oracle_diagnostics(orc):
+    """lbm_stats (FP64 reductions) against the same sums over the oracle's fields."""
+    nx, ny, nz = 24, 20, 16
+    g = inputs.random_deviations(nx, ny, nz, seed=8)
+    s = Solver(nx, ny, nz, nu=0.05)
+    s.set_populations(g)
+    st0 = s.stats()
+    assert st0["residual"] == pytest.approx(1.0)
+    s.step(3)
+    st = s.stats()
+    og = orc.Grid(nx, ny, nz, nu=0.05)
+    rho, u = og.macroscopic(og.step(full(orc, g), 3))
+    assert st["mass"] == pytest.approx(rho.sum(), rel=1e-6)
+    for k, name in enumerate(("mom_x", "mom_y", "mom_z")):
+        assert st[name] == pytest.approx((rho * u[k]).sum(), abs=1e-6 * rho.sum() * 1e-2)
+    assert st["kinetic_energy"] == pytest.approx(orc.kinetic_energy(u), rel=1e-4)
+    assert st["enstrophy"] == pytest.approx(orc.enstrophy(u), rel=1e-4)
+    assert st["fluid_nodes"] == nx * ny * nz
+    assert st["step"] == 3
+    assert 0 < st["residual"] < 10
+
+
+def test_full_size_droplet_sampled(orc):
+    """128^3 Shan-Chen droplet (bench launch configuration): one fused step from a seeded state,
+    checked at 3000 sampled nodes the oracle computes one by one."""
+    N = 128
+    rho = inputs.droplet_density(N, radius=24)
+    g = inputs.random_deviations(N, N, N, seed=9, density=rho)
+    s = Solver(N, N, N, nu=1 / 6)
+    s.set_force("shan_chen", (-5.5,))
+    s.set_populations(g)
+    s.step(1)
+    got = s.get_populations().reshape(27, -1)
+    og = orc.Grid(N, N, N, nu=1 / 6, force_kind=orc.FORCE_SHAN_CHEN, G=-5.5)
+    f = full(orc, g)
+    nodes = np.random.default_rng(10).choice(N ** 3, 3000, replace=False)
+    ref = og.step_sampled(f, nodes) - orc.weights()[None, :]
+    S = scale(orc, f, og)
+    err = np.abs(got[:, nodes].T - ref).max()
+    print(f"droplet 128^3 sampled one-step max error {err:.3e} (S = {S:.3e})")
+    assert err <= C_STEP * EPS32 * S, err
+
+
+def test_divergence_is_reported():
+    """A NaN planted in the host copy of the state is flagged by the step kernel and reported as
+    LBM_ERR_DIVERGED at the next synchronising call (no GPU fault involved)."""
+    g = inputs.random_deviations(16, 8, 8, seed=11)
+    g[3, 2, 4, 5] = np.nan
+    s = Solver(16, 8, 8, nu=0.1)
+    s.set_populations(g)
+    s.step(2)
+    with pytest.raises(LbmError) as e:
+        s.synchronize()
+    assert e.value.status == LBM_ERR_DIVERGED
+    with pytest.raises(LbmError):
+        s.step(1)
+
+
+def test_checkpoint_resume_bit_exact():
+    """2n steps equal n steps + get_populations + set_populations + n steps, bit for bit."""
+    nx, ny, nz = RAGGED
+    g = inputs.random_deviations(nx, ny, nz, seed=12)
+    a = Solver(nx, ny, nz, nu=0.03)
+    a.set_force("uniform", (1e-4, 0, 0))
+    a.set_populations(g)
+    a.step(6)
+    b = Solver(nx, ny, nz, nu=0.03)
+    b.set_force("uniform", (1e-4, 0, 0))
+    b.set_populations(g)
+    b.step(3)
+    mid = b.get_populations()
+    b.set_populations(mid)
+    b.step(3)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+
+
+def test_device_and_host_arguments_agree():
+    """Host (numpy) and device (torch) arrays give identical results through the same calls."""
+    nx, ny, nz = 33, 9, 5
+    g = inputs.random_deviations(nx, ny, nz, seed=13)
+    a = Solver(nx, ny, nz, nu=0.05)
+    a.set_populations(g)
+    b = Solver(nx, ny, nz, nu=0.05)
+    b.set_populations(torch.from_numpy(g).cuda())
+    a.step(2)
+    b.step(2)
+    out = torch.empty((27, nz, ny, nx), dtype=torch.float32, device="cuda")
+    b.get_populations(out)
+    assert np.array_equal(a.get_populations(), out.cpu().numpy())
+    rho = torch.empty((nz, ny, nx), device="cuda")
+    b.macroscopic(rho=rho)
+    ra, *_ = a.macroscopic()
+    assert np.array_equal(ra, rho.cpu().numpy())
