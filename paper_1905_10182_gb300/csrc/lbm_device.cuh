@@ -246,62 +246,147 @@ __device__ __forceinline__ void inverse_fast_dev(const float (&kd)[3][3][3], flo
 }
 
 // ----------------------------------------------------------------------------- collision
-// The time iteration of Sec. II (steps 1-4), on deviations:
-//  1. rho = rho0 + sum g, rho u = sum g c + F/2                       (Eq. macroscopic)
-//  2. k4..k8 from the raw second moments: kappa_ab = Pi_ab - rho u_a u_b + (u_a F_b + u_b F_a)/2
-//                                                                       (Eq. pre_collision)
-//  3. the 19 nonzero post-collision CMs                 (Eq. post_collision_central_moments_forcing)
-//  4. f* = (T^T)^-1 k* through the factorised (fast) CM transform       (Eq. system)
+// The time iteration of Sec. II (steps 1-4), written as an increment so that FP32 rounding
+// scales with the (small) change of each population rather than with the population:
+//   k* - k = Lambda (k^eq - k) + (I - Lambda/2) R        (the post-collision CMs of Sec. II)
+//   f*     = f + (T^T)^-1 (k* - k)                        (Eq. system; T^T is linear)
+// Steps: raw moments of g by three D1Q3 sums; rho, u (Eq. macroscopic); all 27 central moments
+// by three D1Q3 shifts; the increments of Eq. post_collision_central_moments_forcing; the
+// factorised inverse of the increments; g* = g + dg.  The conserved increments are exact by
+// construction: dk_000 = 0 (k0* = k0 = rho) and dk_100 = F_x (k1 = -F_x/2 by Eq. macroscopic,
+// k1* = F_x/2), so mass and momentum move only by rounding of the increment.
 struct Macro {
     float rho, ux, uy, uz;
 };
 
+// One D1Q3 raw-moment sum along an axis: values at c = -1, 0, +1 -> moments 0, 1, 2.
+__device__ __forceinline__ void d1q3_moments(float pm, float p0, float pp, float& m0, float& m1, float& m2) {
+    const float s2 = pp + pm;
+    m0 = s2 + p0;
+    m1 = pp - pm;
+    m2 = s2;
+}
+
+// One D1Q3 shift from raw to central moments about u, in deviation form: inputs are raw moments
+// minus r*(1, 0, 1/3), outputs central moments minus r*(1, 0, 1/3).
+__device__ __forceinline__ void d1q3_shift_dev(float& m0, float& m1, float& m2, float r, float u) {
+    const float A = r + m0;
+    const float c1 = m1 - u * A;
+    const float c2 = m2 - 2.0f * u * m1 + u * u * A;
+    m1 = c1;
+    m2 = c2;
+}
+
+// One D1Q3 inverse without rest state (a linear map): central moments (m0, m1, m2) about u ->
+// values at c = -1, 0, +1.
+__device__ __forceinline__ void d1q3_inverse_lin(float m0, float m1, float m2, float u, float u2, float& pm,
+                                                 float& p0, float& pp) {
+    const float t = m0 * u2 + m2 + 2.0f * u * m1;
+    const float a = m0 * u + m1;
+    p0 = m0 - t;
+    pp = 0.5f * (t + a);
+    pm = 0.5f * (t - a);
+}
+
 __device__ __forceinline__ Macro collide_cm(float (&g)[27], float Fx, float Fy, float Fz, float omega, float rho0) {
-    const RawMoments m = raw_moments(g);
-    const float dr = m.m000;
+    constexpr float s[3] = {1.0f, 0.0f, 1.0f / 3.0f};
+    float K[3][3][3];
+    // raw moments of the deviations: z, then y, then x (index: [x][y][z], each either a velocity
+    // c + 1 or a moment order)
+#pragma unroll
+    for (int i = 0; i < 27; ++i) K[dir_x(i) + 1][dir_y(i) + 1][dir_z(i) + 1] = g[i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) d1q3_moments(K[a][b][0], K[a][b][1], K[a][b][2], K[a][b][0], K[a][b][1], K[a][b][2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d1q3_moments(K[a][0][c], K[a][1][c], K[a][2][c], K[a][0][c], K[a][1][c], K[a][2][c]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d1q3_moments(K[0][b][c], K[1][b][c], K[2][b][c], K[0][b][c], K[1][b][c], K[2][b][c]);
+
+    // step 1: macroscopic variables (Eq. macroscopic)
+    const float dr = K[0][0][0];
     const float rho = rho0 + dr;
     const float inv = 1.0f / rho;
-    const float ux = (m.m100 + 0.5f * Fx) * inv;
-    const float uy = (m.m010 + 0.5f * Fy) * inv;
-    const float uz = (m.m001 + 0.5f * Fz) * inv;
+    const float ux = (K[1][0][0] + 0.5f * Fx) * inv;
+    const float uy = (K[0][1][0] + 0.5f * Fy) * inv;
+    const float uz = (K[0][0][1] + 0.5f * Fz) * inv;
 
-    const float k4 = m.m110 - rho * ux * uy + 0.5f * (ux * Fy + uy * Fx);
-    const float k5 = m.m101 - rho * ux * uz + 0.5f * (ux * Fz + uz * Fx);
-    const float k6 = m.m011 - rho * uy * uz + 0.5f * (uy * Fz + uz * Fy);
-    const float uFx = ux * Fx, uFy = uy * Fy, uFz = uz * Fz;
-    const float k7 = (m.m200 - m.m020) - rho * (ux * ux - uy * uy) + uFx - uFy;
-    const float k8 = (m.m200 - m.m002) - rho * (ux * ux - uz * uz) + uFx - uFz;
+    // step 2: central moments (deviation form), x then y then z shifts
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d1q3_shift_dev(K[0][b][c], K[1][b][c], K[2][b][c], rho0 * s[b] * s[c], ux);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d1q3_shift_dev(K[a][0][c], K[a][1][c], K[a][2][c], rho0 * s[a] * s[c], uy);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) d1q3_shift_dev(K[a][b][0], K[a][b][1], K[a][b][2], rho0 * s[a] * s[b], uz);
 
+    // step 3: increments k* - k.  k4..k6 = kappa_110, 101, 011 relax at omega; k7 = k200 - k020,
+    // k8 = k200 - k002 at omega; k9 = k200 + k020 + k002 -> rho; every other moment goes to its
+    // post-collision value of Eq. post_collision_central_moments_forcing (rate 1).
+    const float k7 = K[2][0][0] - K[0][2][0];
+    const float k8 = K[2][0][0] - K[0][0][2];
     const float om1 = 1.0f - omega;
-    const float k4s = om1 * k4, k5s = om1 * k5, k6s = om1 * k6, k7s = om1 * k7, k8s = om1 * k8;
-
-    // kappa*_abc from k*: k7 = k200 - k020, k8 = k200 - k002, k9 = k200 + k020 + k002 = rho;
-    // k10/k13 -> k120 = k102 = Fx c_s^2/2 (and cyclic); k17..k19 -> k220 = k202 = k022 = rho c_s^4;
-    // k23..k25 -> k122 = Fx c_s^4/2 (and cyclic); k26 = k222 = rho c_s^6.  Deviations from rest.
+    const float k7s = om1 * k7, k8s = om1 * k8;
     const float third = 1.0f / 3.0f;
-    float kd[3][3][3];
-    kd[0][0][0] = dr;
-    kd[1][0][0] = 0.5f * Fx;
-    kd[0][1][0] = 0.5f * Fy;
-    kd[0][0][1] = 0.5f * Fz;
-    kd[1][1][0] = k4s;
-    kd[1][0][1] = k5s;
-    kd[0][1][1] = k6s;
-    kd[2][0][0] = (k7s + k8s + dr) * third;
-    kd[0][2][0] = (dr - 2.0f * k7s + k8s) * third;
-    kd[0][0][2] = (dr + k7s - 2.0f * k8s) * third;
-    kd[1][2][0] = kd[1][0][2] = Fx * (1.0f / 6.0f);
-    kd[2][1][0] = kd[0][1][2] = Fy * (1.0f / 6.0f);
-    kd[2][0][1] = kd[0][2][1] = Fz * (1.0f / 6.0f);
-    kd[1][1][1] = 0.0f;
-    kd[2][2][0] = kd[2][0][2] = kd[0][2][2] = dr * (1.0f / 9.0f);
-    kd[2][1][1] = kd[1][2][1] = kd[1][1][2] = 0.0f;
-    kd[1][2][2] = Fx * (1.0f / 18.0f);
-    kd[2][1][2] = Fy * (1.0f / 18.0f);
-    kd[2][2][1] = Fz * (1.0f / 18.0f);
-    kd[2][2][2] = dr * (1.0f / 27.0f);
+    K[0][0][0] = 0.0f;
+    K[1][0][0] = Fx;
+    K[0][1][0] = Fy;
+    K[0][0][1] = Fz;
+    K[1][1][0] = -omega * K[1][1][0];
+    K[1][0][1] = -omega * K[1][0][1];
+    K[0][1][1] = -omega * K[0][1][1];
+    K[2][0][0] = (k7s + k8s + dr) * third - K[2][0][0];
+    K[0][2][0] = (dr - 2.0f * k7s + k8s) * third - K[0][2][0];
+    K[0][0][2] = (dr + k7s - 2.0f * k8s) * third - K[0][0][2];
+    const float fx6 = Fx * (1.0f / 6.0f), fy6 = Fy * (1.0f / 6.0f), fz6 = Fz * (1.0f / 6.0f);
+    K[1][2][0] = fx6 - K[1][2][0];
+    K[1][0][2] = fx6 - K[1][0][2];
+    K[2][1][0] = fy6 - K[2][1][0];
+    K[0][1][2] = fy6 - K[0][1][2];
+    K[2][0][1] = fz6 - K[2][0][1];
+    K[0][2][1] = fz6 - K[0][2][1];
+    K[1][1][1] = -K[1][1][1];
+    const float dr9 = dr * (1.0f / 9.0f);
+    K[2][2][0] = dr9 - K[2][2][0];
+    K[2][0][2] = dr9 - K[2][0][2];
+    K[0][2][2] = dr9 - K[0][2][2];
+    K[2][1][1] = -K[2][1][1];
+    K[1][2][1] = -K[1][2][1];
+    K[1][1][2] = -K[1][1][2];
+    K[1][2][2] = Fx * (1.0f / 18.0f) - K[1][2][2];
+    K[2][1][2] = Fy * (1.0f / 18.0f) - K[2][1][2];
+    K[2][2][1] = Fz * (1.0f / 18.0f) - K[2][2][1];
+    K[2][2][2] = dr * (1.0f / 27.0f) - K[2][2][2];
 
-    inverse_fast_dev(kd, ux, uy, uz, rho0, g);
+    // step 4: dg = (T^T)^-1 dk, z then y then x inverses; g* = g + dg
+    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            d1q3_inverse_lin(K[a][b][0], K[a][b][1], K[a][b][2], uz, uz2, K[a][b][0], K[a][b][1], K[a][b][2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            d1q3_inverse_lin(K[a][0][c], K[a][1][c], K[a][2][c], uy, uy2, K[a][0][c], K[a][1][c], K[a][2][c]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            d1q3_inverse_lin(K[0][b][c], K[1][b][c], K[2][b][c], ux, ux2, K[0][b][c], K[1][b][c], K[2][b][c]);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) g[i] += K[dir_x(i) + 1][dir_y(i) + 1][dir_z(i) + 1];
     return Macro{rho, ux, uy, uz};
 }
 
