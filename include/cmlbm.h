@@ -161,6 +161,28 @@ LBM_API long long lbm_time(const lbm_ctx* ctx);
 LBM_API const char* lbm_last_error(const lbm_ctx* ctx);
 LBM_API const char* lbm_status_string(int status);
 
+/* Allocation-free FP64 diagnostics (the paper has no counterpart; this is a library service).
+ * For callers that must not allocate device memory on their hot path -- a framework whose
+ * caching allocator owns the device's memory budget, or a loop that cannot afford the implicit
+ * device synchronisation of cudaMalloc/cudaFree.  It computes what lbm_stats computes, but over
+ * fields the caller passes in, and it allocates nothing: its scratch is a fixed device array
+ * inside the library (room for the partial sums of 1216 reduction blocks, about 88 KB, held by
+ * every device that loads the library until the process exits).
+ *   nx, ny, nz, walls_y: grid as in lbm_desc; N = nx*ny*nz must be < 2^31 (else LBM_ERR_ARG).
+ *   mask: NULL or N device bytes, nonzero = solid (excluded).
+ *   rho, ux, uy, uz: N device floats each (e.g. filled by lbm_macroscopic).
+ *   uprev: NULL (residual = 1) or 3N device floats (ux, uy, uz blocks) of an earlier state.
+ *   out: LBM_STATS_LEN - 1 doubles, host or device: entries [0..8] of the lbm_stats layout.
+ *   stream: cudaStream_t (NULL = legacy default); the call waits for it before returning.
+ * The first call on each device looks up the scratch array's device address (with that device
+ * current); make that first call before any stream capture.  All calls on a device share the
+ * one scratch array, so calls whose kernels overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller.  Every value it reads back is rewritten by the same
+ * call, so nothing needs clearing between calls. */
+LBM_API lbm_status lbm_reduce_fields_noalloc(int nx, int ny, int nz, int walls_y, const uint8_t* mask,
+                                             const float* rho, const float* ux, const float* uy, const float* uz,
+                                             const float* uprev, double* out, void* stream);
+
 /* Frees everything the library allocated for ctx.  NULL is ignored.  Waits for the stream. */
 LBM_API void lbm_destroy(lbm_ctx* ctx);
 

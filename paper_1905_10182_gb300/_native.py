@@ -81,6 +81,9 @@ def lib():
         L.lbm_profile.restype = st
         L.lbm_profile_read.argtypes = [_P, ctypes.POINTER(ctypes.c_double)]
         L.lbm_profile_read.restype = st
+        L.lbm_reduce_fields_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                                _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]
+        L.lbm_reduce_fields_noalloc.restype = st
         L.lbm_time.argtypes = [_P]
         L.lbm_time.restype = ctypes.c_longlong
         L.lbm_last_error.argtypes = [_P]
