@@ -143,10 +143,11 @@ LBM_API lbm_status lbm_stats(lbm_ctx* ctx, double* out);
 /* Waits for the stream; LBM_ERR_DIVERGED if a step since the last check flagged a node. */
 LBM_API lbm_status lbm_synchronize(lbm_ctx* ctx);
 
-/* Kernel timing hook for benchmarks: while enabled, lbm_step records a CUDA event pair on the
- * context's stream around every stream-collide launch and every psi launch.  It changes no
- * result; the cost is two event records per launch. */
-LBM_API lbm_status lbm_profile(lbm_ctx* ctx, int enable);
+/* Kernel timing hook for benchmarks: with every >= 1, lbm_step records a CUDA event pair on the
+ * context's stream around the stream-collide launch and the psi launch of every every-th step
+ * (every = 0 turns it off).  It changes no result; the cost is two event records per timed
+ * launch. */
+LBM_API lbm_status lbm_profile(lbm_ctx* ctx, int every);
 
 #define LBM_PROFILE_LEN 4
 /* Waits for the stream, then returns and clears the totals gathered since the last read

@@ -47,7 +47,7 @@ struct lbm_ctx {
     unsigned int* flag_dev = nullptr;
     unsigned int* flag_host = nullptr;  // pinned
 
-    bool profile = false;
+    int profile = 0;  // record kernel timings of every profile-th step (0: off)
     std::vector<cudaEvent_t> events;  // pool, reused after each read
     std::vector<int> event_kind;      // per recorded pair: 0 stream-collide, 1 psi
     size_t events_used = 0;           // events recorded since the last read (pairs * 2)
@@ -214,7 +214,7 @@ lbm_status run_macro(lbm_ctx* c) {
 
 // Records one event of a timing pair when profiling is on.
 lbm_status profile_mark(lbm_ctx* c, int kind) {
-    if (!c->profile) return LBM_OK;
+    if (c->profile <= 0 || (c->t % c->profile) != 0) return LBM_OK;
     if (c->events_used == c->events.size()) {
         cudaEvent_t e;
         CK(c, cudaEventCreate(&e), "cudaEventCreate");
@@ -525,9 +525,10 @@ lbm_status lbm_synchronize(lbm_ctx* c) {
     return sync_and_check(c);
 }
 
-lbm_status lbm_profile(lbm_ctx* c, int enable) {
+lbm_status lbm_profile(lbm_ctx* c, int every) {
     if (!c) return LBM_ERR_ARG;
-    c->profile = enable != 0;
+    if (every < 0) return fail(c, LBM_ERR_ARG, "every must be >= 0");
+    c->profile = every;
     return LBM_OK;
 }
 

@@ -288,13 +288,14 @@ __device__ __forceinline__ void d1q3_inverse_lin(float m0, float m1, float m2, f
     pm = 0.5f * (t - a);
 }
 
-__device__ __forceinline__ Macro collide_cm(float (&g)[27], float Fx, float Fy, float Fz, float omega, float rho0) {
+// In: K[x][y][z] holds the deviations g arranged by velocity (index c + 1).  Out: K holds the
+// increments dg arranged the same way.  Returns rho and u of the node.
+__device__ __forceinline__ Macro collide_increment(float (&K)[3][3][3], float Fx, float Fy, float Fz, float omega,
+                                                   float rho0) {
     constexpr float s[3] = {1.0f, 0.0f, 1.0f / 3.0f};
-    float K[3][3][3];
+
     // raw moments of the deviations: z, then y, then x (index: [x][y][z], each either a velocity
     // c + 1 or a moment order)
-#pragma unroll
-    for (int i = 0; i < 27; ++i) K[dir_x(i) + 1][dir_y(i) + 1][dir_z(i) + 1] = g[i];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -385,9 +386,17 @@ __device__ __forceinline__ Macro collide_cm(float (&g)[27], float Fx, float Fy, 
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             d1q3_inverse_lin(K[0][b][c], K[1][b][c], K[2][b][c], ux, ux2, K[0][b][c], K[1][b][c], K[2][b][c]);
+    return Macro{rho, ux, uy, uz};
+}
+
+__device__ __forceinline__ Macro collide_cm(float (&g)[27], float Fx, float Fy, float Fz, float omega, float rho0) {
+    float K[3][3][3];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) K[dir_x(i) + 1][dir_y(i) + 1][dir_z(i) + 1] = g[i];
+    const Macro m = collide_increment(K, Fx, Fy, Fz, omega, rho0);
 #pragma unroll
     for (int i = 0; i < 27; ++i) g[i] += K[dir_x(i) + 1][dir_y(i) + 1][dir_z(i) + 1];
-    return Macro{rho, ux, uy, uz};
+    return m;
 }
 
 // Equilibrium deviations g_i = f_i^eq(rho, u) - w_i rho0: the equilibrium CMs of

@@ -131,8 +131,9 @@ class Solver:
                 "fluid_nodes", "step")
         return dict(zip(keys, list(out)))
 
-    def profile(self, enable=True):
-        self._check(self._lib.lbm_profile(self._h, int(bool(enable))))
+    def profile(self, every=1):
+        """Record kernel times of every every-th step (0: off)."""
+        self._check(self._lib.lbm_profile(self._h, int(every)))
 
     def profile_read(self):
         out = (ctypes.c_double * nat.LBM_PROFILE_LEN)()
