@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="droplet128")
     ap.add_argument("--storage", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--n", type=int, default=None, help="override the cube edge (profiling of smaller cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -372,7 +373,12 @@ def run_ours(args, wl):
 
 def main():
     args = parse()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.n:
+        if wl["kind"] == "droplet":
+            wl["radius"] = wl["radius"] * args.n / wl["n"]
+        wl["text"] = wl["text"].replace(f"{wl['n']}^3", f"{args.n}^3")
+        wl["n"] = args.n
     if args.impl == "reference":
         run_reference(args, wl)
     else:
