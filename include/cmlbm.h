@@ -162,6 +162,58 @@ LBM_API long long lbm_time(const lbm_ctx* ctx);
 LBM_API const char* lbm_last_error(const lbm_ctx* ctx);
 LBM_API const char* lbm_status_string(int status);
 
+/* ------------------------------------------------------------------------------------------
+ * Batched solver: many independent domains, each with its own grid, nu, constant force, walls
+ * and solid mask, advanced together by one persistent kernel launch per time step over a
+ * device-resident tile list, replayed from a captured CUDA graph.  The per-node step is the one
+ * of lbm_step (Sec. II, FP32 storage), so each domain evolves exactly as a single domain would.
+ * A domain whose FP64 residual r = |u^n - u^(n-D)|_2 / (D |u^n|_2) -- the mean relative velocity
+ * change per step over the window D = check_every, norms over fluid nodes -- falls to tol is
+ * retired: its state is frozen and it leaves the tile list.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch;
+
+typedef struct {
+    int nx, ny, nz;        /* grid, N = nx*ny*nz < 2^31                                           */
+    double nu;             /* viscosity > 0                                                        */
+    double force[3];       /* constant force density                                               */
+    int walls_y;           /* halfway bounce-back walls at y = -1/2 and ny - 1/2                   */
+    const uint8_t* mask;   /* NULL or N bytes (host or device), nonzero = solid; copied            */
+} lbm_domain;
+
+/* Creates the batch (all domains at rest: rho = rho0, u = 0) on the current device and stream.
+ * Population memory: 108 B per node in one pool, plus 16 B per node (links, previous u). */
+LBM_API lbm_status lbm_batch_create(const lbm_domain* domains, int count, double rho0, void* stream, lbm_batch** out);
+
+/* Times trial_steps (rounded to even, >= 2) graph-replayed steps for each candidate launch shape
+ * (64, 128, 256 nodes per tile; 1/2x, 1x, 4x the resident blocks per SM) and keeps the fastest.
+ * out (optional, 3 doubles): best MLUPS, nodes per tile, blocks per SM.  The trials advance the
+ * state, so afterwards every domain is reset to rest: call it before lbm_batch_set_state. */
+LBM_API lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, double* out);
+
+/* Enqueues nsteps steps of every active domain. */
+LBM_API lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
+
+/* Steps the active domains in graph-replayed chunks of check_every (even, >= 2) steps until each
+ * reaches residual <= tol (after at least two checks), diverges, or max_steps elapse.  Per domain
+ * (arrays of count, optional): steps[k] = steps taken at retirement (or at the end), residual[k]
+ * = last residual, status[k] = 0 steady, 1 not steady after max_steps, 2 diverged. */
+LBM_API lbm_status lbm_batch_run(lbm_batch* b, double tol, long long max_steps, int check_every, long long* steps,
+                                 double* residual, int* status);
+
+/* f = f^eq(rho, u) for domain k (arrays of N floats, host or device); needs even batch parity. */
+LBM_API lbm_status lbm_batch_set_state(lbm_batch* b, int k, const float* rho, const float* ux, const float* uy,
+                                       const float* uz);
+/* rho, u (with F/2) of domain k; any output may be NULL; host or device; waits for the stream. */
+LBM_API lbm_status lbm_batch_macroscopic(lbm_batch* b, int k, float* rho, float* ux, float* uy, float* uz);
+/* Populations of domain k as FP32 deviations in natural order (27 * N floats, host or device). */
+LBM_API lbm_status lbm_batch_get_populations(lbm_batch* b, int k, float* g);
+LBM_API long long lbm_batch_nodes(const lbm_batch* b);
+LBM_API long long lbm_batch_time(const lbm_batch* b);
+LBM_API int lbm_batch_active(const lbm_batch* b);
+LBM_API const char* lbm_batch_last_error(const lbm_batch* b);
+LBM_API void lbm_batch_destroy(lbm_batch* b);
+
 /* Allocation-free FP64 diagnostics (the paper has no counterpart; this is a library service).
  * For callers that must not allocate device memory on their hot path -- a framework whose
  * caching allocator owns the device's memory budget, or a loop that cannot afford the implicit

@@ -5,4 +5,4 @@ The compute path is the CUDA library libcmlbm.so (C ABI in include/cmlbm.h); ``S
 thin binding over it.  ``build()`` compiles the library for sm_103a.
 """
 from .buildlib import build  # noqa: F401
-from .solver import Solver  # noqa: F401
+from .solver import BatchSolver, Solver  # noqa: F401

@@ -33,6 +33,16 @@ class LbmDesc(ctypes.Structure):
     ]
 
 
+class LbmDomain(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("nu", ctypes.c_double),
+        ("force", ctypes.c_double * 3),
+        ("walls_y", ctypes.c_int),
+        ("mask", ctypes.c_void_p),
+    ]
+
+
 class LbmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{status_name(status)}: {msg}")
@@ -84,6 +94,32 @@ def lib():
         L.lbm_reduce_fields_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                                 _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]
         L.lbm_reduce_fields_noalloc.restype = st
+        L.lbm_batch_create.argtypes = [ctypes.POINTER(LbmDomain), ctypes.c_int, ctypes.c_double, _P, ctypes.POINTER(_P)]
+        L.lbm_batch_create.restype = st
+        L.lbm_batch_autotune.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        L.lbm_batch_autotune.restype = st
+        L.lbm_batch_step.argtypes = [_P, ctypes.c_int]
+        L.lbm_batch_step.restype = st
+        L.lbm_batch_run.argtypes = [_P, ctypes.c_double, ctypes.c_longlong, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_int)]
+        L.lbm_batch_run.restype = st
+        L.lbm_batch_set_state.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
+        L.lbm_batch_set_state.restype = st
+        L.lbm_batch_macroscopic.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
+        L.lbm_batch_macroscopic.restype = st
+        L.lbm_batch_get_populations.argtypes = [_P, ctypes.c_int, _P]
+        L.lbm_batch_get_populations.restype = st
+        L.lbm_batch_nodes.argtypes = [_P]
+        L.lbm_batch_nodes.restype = ctypes.c_longlong
+        L.lbm_batch_time.argtypes = [_P]
+        L.lbm_batch_time.restype = ctypes.c_longlong
+        L.lbm_batch_active.argtypes = [_P]
+        L.lbm_batch_active.restype = ctypes.c_int
+        L.lbm_batch_last_error.argtypes = [_P]
+        L.lbm_batch_last_error.restype = ctypes.c_char_p
+        L.lbm_batch_destroy.argtypes = [_P]
+        L.lbm_batch_destroy.restype = None
         L.lbm_time.argtypes = [_P]
         L.lbm_time.restype = ctypes.c_longlong
         L.lbm_last_error.argtypes = [_P]

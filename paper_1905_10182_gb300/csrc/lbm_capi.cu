@@ -69,6 +69,7 @@ lbm_status fail(lbm_ctx* c, lbm_status st, const std::string& msg) {
 }
 
 lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+    cudaGetLastError();  // consume the error so that later, unrelated launches do not report it
     std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
 }

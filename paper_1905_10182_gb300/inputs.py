@@ -89,14 +89,16 @@ def taylor_green(n, u0, rho0=1.0):
 def sphere_pack(nx, ny, nz, seed, phi_max=0.2, rmin=3, rmax=8, max_tries=2000):
     """Random non-overlapping spheres (radii uniform in [rmin, rmax], centres uniform, rejection
     on overlap) added until the solid fraction reaches a target drawn uniformly in [0, phi_max].
-    Returns (mask uint8 (nz, ny, nx), target fraction).  Periodic in x and z."""
+    Returns (mask uint8 (nz, ny, nx), target fraction).  Periodic in x and z; sphere centres keep
+    a radius away from the y walls."""
     rng = SplitMix(seed)
     target = rng.uniform(0.0, phi_max)
     mask = np.zeros((nz, ny, nx), dtype=np.uint8)
     spheres = []
-    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    solid = 0
+    total = nx * ny * nz
     tries = 0
-    while mask.mean() < target and tries < max_tries:
+    while solid < target * total and tries < max_tries:
         tries += 1
         r = rng.integer(rmin, rmax)
         cx, cy, cz = rng.uniform(0, nx), rng.uniform(r, max(r, ny - r)), rng.uniform(0, nz)
@@ -110,9 +112,16 @@ def sphere_pack(nx, ny, nz, seed, phi_max=0.2, rmin=3, rmax=8, max_tries=2000):
         if not ok:
             continue
         spheres.append((cx, cy, cz, r))
-        dx = np.minimum(np.abs(x - cx), nx - np.abs(x - cx))
-        dz = np.minimum(np.abs(z - cz), nz - np.abs(z - cz))
-        mask |= ((dx * dx + (y - cy) ** 2 + dz * dz) <= r * r).astype(np.uint8)
+        # nodes of the bounding box, with periodic wrap in x and z
+        xs = np.arange(int(math.floor(cx - r)), int(math.ceil(cx + r)) + 1)
+        ys = np.arange(max(0, int(math.floor(cy - r))), min(ny - 1, int(math.ceil(cy + r))) + 1)
+        zs = np.arange(int(math.floor(cz - r)), int(math.ceil(cz + r)) + 1)
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        inside = (X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2 <= r * r
+        zi, yi, xi = Z[inside] % nz, Y[inside], X[inside] % nx
+        before = int(mask[zi, yi, xi].sum())
+        mask[zi, yi, xi] = 1
+        solid += int(mask[zi, yi, xi].sum()) - before
     return mask, target
 
 

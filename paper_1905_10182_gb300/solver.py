@@ -146,3 +146,96 @@ class Solver:
     @property
     def time(self):
         return self._lib.lbm_time(self._h)
+
+
+class BatchSolver:
+    """Many independent domains advanced together (lbm_batch_* of the C ABI)."""
+
+    def __init__(self, domains, rho0=1.0, stream=None):
+        """domains: list of dicts with nx, ny, nz, nu, and optional force (3-tuple), walls_y, mask."""
+        self._lib = nat.lib()
+        n = len(domains)
+        arr = (nat.LbmDomain * n)()
+        self._masks = []
+        self.shapes = []
+        for k, d in enumerate(domains):
+            a = arr[k]
+            a.nx, a.ny, a.nz = int(d["nx"]), int(d["ny"]), int(d["nz"])
+            a.nu = float(d["nu"])
+            f = d.get("force", (0.0, 0.0, 0.0))
+            for j in range(3):
+                a.force[j] = float(f[j])
+            a.walls_y = int(bool(d.get("walls_y", False)))
+            m = d.get("mask")
+            if m is not None:
+                m = np.ascontiguousarray(m, dtype=np.uint8)
+                self._masks.append(m)
+                a.mask = m.ctypes.data
+            self.shapes.append((a.nz, a.ny, a.nx))
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = ctypes.c_void_p()
+        st = self._lib.lbm_batch_create(arr, n, float(rho0), ctypes.c_void_p(int(stream)) if stream else None,
+                                        ctypes.byref(h))
+        if st != nat.LBM_OK:
+            raise nat.LbmError(st, "lbm_batch_create failed")
+        self._h = h
+        self.count = n
+
+    def _check(self, st):
+        if st != nat.LBM_OK:
+            raise nat.LbmError(st, self._lib.lbm_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nodes(self):
+        return self._lib.lbm_batch_nodes(self._h)
+
+    @property
+    def active(self):
+        return self._lib.lbm_batch_active(self._h)
+
+    @property
+    def time(self):
+        return self._lib.lbm_batch_time(self._h)
+
+    def autotune(self, trial_steps=20):
+        out = (ctypes.c_double * 3)()
+        self._check(self._lib.lbm_batch_autotune(self._h, int(trial_steps), out))
+        return dict(mlups=out[0], tile=int(out[1]), blocks_per_sm=int(out[2]))
+
+    def step(self, nsteps=1):
+        self._check(self._lib.lbm_batch_step(self._h, int(nsteps)))
+
+    def run(self, tol=1e-8, max_steps=100000, check_every=100):
+        n = self.count
+        steps = (ctypes.c_longlong * n)()
+        res = (ctypes.c_double * n)()
+        status = (ctypes.c_int * n)()
+        self._check(self._lib.lbm_batch_run(self._h, float(tol), int(max_steps), int(check_every), steps, res, status))
+        return np.array(steps[:]), np.array(res[:]), np.array(status[:])
+
+    def set_state(self, k, rho, ux, uy, uz):
+        arrs = [_f32(a) for a in (rho, ux, uy, uz)]
+        self._check(self._lib.lbm_batch_set_state(self._h, int(k), *(nat.ptr(a) for a in arrs)))
+
+    def macroscopic(self, k):
+        outs = [np.empty(self.shapes[k], dtype=np.float32) for _ in range(4)]
+        self._check(self._lib.lbm_batch_macroscopic(self._h, int(k), *(nat.ptr(a) for a in outs)))
+        return outs
+
+    def get_populations(self, k):
+        out = np.empty((27,) + self.shapes[k], dtype=np.float32)
+        self._check(self._lib.lbm_batch_get_populations(self._h, int(k), nat.ptr(out)))
+        return out

@@ -1,0 +1,99 @@
+"""Batched solver (lbm_batch_*): uneven domains advanced by one persistent launch per step.
+
+Each batch domain must evolve exactly as the same domain run alone (same per-node arithmetic), and
+match the FP64 oracle within the per-step bound of test_gpu_parity; run-to-steady retires converged
+domains; the autotuner returns a valid shape and leaves the batch at rest.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1905_10182_gb300 import BatchSolver, Solver, inputs  # noqa: E402
+
+EPS32 = 2.0 ** -24
+
+
+def _domains():
+    rng = np.random.default_rng(31)
+    doms = []
+    for k, (nx, ny, nz) in enumerate([(19, 13, 11), (32, 16, 8), (7, 21, 5), (40, 9, 13), (16, 16, 16)]):
+        mask = inputs.random_mask(nx, ny, nz, seed=40 + k, fraction=0.12) if k % 2 == 0 else None
+        doms.append(dict(nx=nx, ny=ny, nz=nz, nu=float(rng.uniform(0.02, 0.15)),
+                         force=(float(rng.uniform(1e-5, 1e-4)), 0.0, float(rng.uniform(-1e-5, 1e-5))),
+                         walls_y=bool(k != 4), mask=mask))
+    return doms
+
+
+def test_batch_domains_match_single_domain_runs():
+    doms = _domains()
+    b = BatchSolver(doms)
+    b.step(7)
+    for k, d in enumerate(doms):
+        s = Solver(d["nx"], d["ny"], d["nz"], nu=d["nu"], walls_y=d["walls_y"], mask=d["mask"])
+        s.set_force("uniform", d["force"])
+        s.step(7)
+        assert np.array_equal(b.get_populations(k), s.get_populations()), k
+
+
+def test_batch_domain_matches_oracle(orc):
+    doms = _domains()
+    b = BatchSolver(doms)
+    for k in (0, 3):
+        d = doms[k]
+        rho = np.ones((d["nz"], d["ny"], d["nx"]), np.float32) * 1.02
+        u = np.zeros((3,) + rho.shape, np.float32)
+        u[0] = 0.01
+        b.set_state(k, rho, u[0], u[1], u[2])
+    b.step(3)
+    for k in (0, 3):
+        d = doms[k]
+        og = orc.Grid(d["nx"], d["ny"], d["nz"], nu=d["nu"], walls_y=d["walls_y"], mask=d["mask"],
+                      collision=orc.COLL_PAPER, force_kind=orc.FORCE_UNIFORM, force=d["force"])
+        rho = np.full((d["nz"], d["ny"], d["nx"]), 1.02)
+        u = np.zeros((3,) + rho.shape)
+        u[0] = 0.01
+        f = og.step(og.init_equilibrium(rho.astype(np.float32).astype(np.float64),
+                                        u.astype(np.float32).astype(np.float64)), 3)
+        ref = f - orc.weights()[:, None, None, None]
+        fluid = np.ones(rho.shape, bool) if d["mask"] is None else d["mask"] == 0
+        err = np.abs(b.get_populations(k) - ref)[:, fluid].max()
+        assert err <= 3 * 64 * EPS32 * 0.05, (k, err)
+
+
+def test_batch_run_to_steady_retires_domains():
+    """Clean channels of three heights: each reaches residual 1e-8 and retires; the steady profile
+    is the halfway-bounce-back Poiseuille parabola to second-order accuracy."""
+    doms = [dict(nx=4, ny=H, nz=4, nu=0.1, force=(1e-6, 0, 0), walls_y=True) for H in (8, 12, 16)]
+    b = BatchSolver(doms)
+    steps, res, status = b.run(tol=1e-8, max_steps=40000, check_every=100)
+    assert (status == 0).all(), (steps, res, status)
+    assert steps[0] < steps[1] < steps[2]  # wider channels relax more slowly (rate nu (pi/H)^2)
+    assert b.active == 0
+    for k, H in enumerate((8, 12, 16)):
+        _, ux, _, _ = b.macroscopic(k)
+        y = np.arange(H) + 0.5
+        ex = 1e-6 / (2 * 0.1) * y * (H - y)
+        err = np.abs(ux[0, :, 0] - ex).max() / ex.max()
+        assert err < 3.0 / H ** 2, (H, err)
+
+
+def test_batch_autotune_resets_to_rest():
+    doms = _domains()
+    b = BatchSolver(doms)
+    out = b.autotune(trial_steps=4)
+    assert out["tile"] in (64, 128, 256) and out["blocks_per_sm"] >= 1 and out["mlups"] > 0
+    assert b.time == 0
+    for k in range(len(doms)):
+        assert np.abs(b.get_populations(k)).max() == 0.0
+    b.step(7)  # results after tuning equal the default shape's results
+    s = Solver(doms[1]["nx"], doms[1]["ny"], doms[1]["nz"], nu=doms[1]["nu"], walls_y=doms[1]["walls_y"])
+    s.set_force("uniform", doms[1]["force"])
+    s.step(7)
+    assert np.array_equal(b.get_populations(1), s.get_populations())
