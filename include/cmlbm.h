@@ -214,6 +214,22 @@ LBM_API int lbm_batch_active(const lbm_batch* b);
 LBM_API const char* lbm_batch_last_error(const lbm_batch* b);
 LBM_API void lbm_batch_destroy(lbm_batch* b);
 
+/* ------------------------------------------------------------------------------------------
+ * Neural-operator warm start (no counterpart in the paper: a learned initial condition for the
+ * steady solves of the batched solver; the plain CM-LBM run to the same residual judges it).
+ * ------------------------------------------------------------------------------------------ */
+
+/* BF16 tensor-core GEMM (tcgen05, FP32 accumulation), the contraction every layer of the neural
+ * operator runs on:  C[b] = alpha * A[b] x B[b]  (beta != 0: C[b] += ...),  b < batch.
+ * Element (m, k) of A[b] is at A + b*sab + m*sam + k*sak (BF16 elements), (k, n) of B at
+ * B + b*sbb + k*sbk + n*sbn, (m, n) of C at C + b*scb + m*scm + n*scn (FP32, or BF16 with
+ * out_bf16).  All pointers are device memory; err is a device flag set to 1 if an internal
+ * bounded wait timed out.  Enqueued on stream; LBM_ERR_ARG on bad sizes. */
+LBM_API lbm_status lbm_gemm_bf16(int M, int N, int K, int batch, const void* A, long long sam, long long sak,
+                                 long long sab, const void* B, long long sbk, long long sbn, long long sbb, void* C,
+                                 long long scm, long long scn, long long scb, int out_bf16, float alpha, int beta,
+                                 unsigned int* err, void* stream);
+
 /* Allocation-free FP64 diagnostics (the paper has no counterpart; this is a library service).
  * For callers that must not allocate device memory on their hot path -- a framework whose
  * caching allocator owns the device's memory budget, or a loop that cannot afford the implicit

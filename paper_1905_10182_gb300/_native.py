@@ -120,6 +120,12 @@ def lib():
         L.lbm_batch_last_error.restype = ctypes.c_char_p
         L.lbm_batch_destroy.argtypes = [_P]
         L.lbm_batch_destroy.restype = None
+        L.lbm_gemm_bf16.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    _P, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong,
+                                    _P, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong,
+                                    _P, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong,
+                                    ctypes.c_int, ctypes.c_float, ctypes.c_int, _P, _P]
+        L.lbm_gemm_bf16.restype = st
         L.lbm_time.argtypes = [_P]
         L.lbm_time.restype = ctypes.c_longlong
         L.lbm_last_error.argtypes = [_P]

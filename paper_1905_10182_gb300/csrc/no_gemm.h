@@ -1,0 +1,28 @@
+// Launch interface of the BF16 tensor-core GEMM (no_gemm.cu) used by the neural operator.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace cmlbm {
+
+// C[b] (+)= alpha * A[b] x B[b].  Element (m, k) of A[b] is A[b * sab + m * sam + k * sak], likewise
+// B (k, n) and C (m, n).  A and B are BF16; C is FP32, or BF16 when out_bf16 is set.  beta != 0
+// adds to the existing C.  err: device flag set to 1 if an mbarrier wait timed out.
+struct GemmArgs {
+    int M, N, K;
+    const __nv_bfloat16* A;
+    long long sam, sak, sab;
+    const __nv_bfloat16* B;
+    long long sbk, sbn, sbb;
+    void* C;
+    long long scm, scn, scb;
+    int out_bf16;
+    float alpha;
+    int beta;
+    unsigned int* err;
+};
+
+cudaError_t launch_gemm_bf16(const GemmArgs& g, int batch, cudaStream_t st);
+
+}  // namespace cmlbm

@@ -1,0 +1,73 @@
+"""The tcgen05 BF16 GEMM (lbm_gemm_bf16) against an FP64 product of the same BF16 inputs.
+
+Bound: FP32 accumulation of K exact BF16 products, |C - C_ref| <= 2^-20 * sum_k |a_mk| |b_kn|
+(per element), which covers any summation order of the tensor core's FP32 adds.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1905_10182_gb300 import _native as nat  # noqa: E402
+
+
+def _gemm(M, N, K, batch, A, sa, B, sb, C, sc, out_bf16=0, alpha=1.0, beta=0):
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = nat.lib().lbm_gemm_bf16(M, N, K, batch, A.data_ptr(), *sa, B.data_ptr(), *sb, C.data_ptr(), *sc,
+                                 out_bf16, ctypes.c_float(alpha), beta, err.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream)
+    assert st == nat.LBM_OK, nat.status_name(st)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+
+
+def _check(Cg, Cr, bound):
+    diff = np.abs(Cg - Cr)
+    assert (diff <= bound + 1e-30).all(), (diff.max(), bound.max())
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (300, 100, 150), (7, 5, 3), (256, 192, 512)])
+def test_gemm_row_major(M, N, K):
+    g = torch.Generator().manual_seed(M * 7 + N)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(K, N, generator=g).to(torch.bfloat16)
+    C = torch.empty(M, N, device="cuda")
+    Ad, Bd = A.cuda(), B.cuda()
+    _gemm(M, N, K, 1, Ad, (K, 1, 0), Bd, (N, 1, 0), C, (N, 1, 0))
+    a, b = A.float().numpy().astype(np.float64), B.float().numpy().astype(np.float64)
+    _check(C.cpu().numpy(), a @ b, 2.0 ** -20 * (np.abs(a) @ np.abs(b)))
+
+
+def test_gemm_transposed_batched_views():
+    """A as an M-contiguous view, B K-contiguous (N x K storage), C column-major, batch 3."""
+    M, N, K, nb = 200, 72, 96, 3
+    g = torch.Generator().manual_seed(5)
+    At = torch.randn(nb, K, M, generator=g).to(torch.bfloat16)  # A[b][m][k] = At[b][k][m]
+    Bt = torch.randn(nb, N, K, generator=g).to(torch.bfloat16)  # B[b][k][n] = Bt[b][n][k]
+    C = torch.zeros(nb, N, M, device="cuda")                      # C[b][m][n] at (n, m)
+    _gemm(M, N, K, nb, At.cuda(), (1, M, K * M), Bt.cuda(), (1, K, N * K), C, (1, M, N * M))
+    for i in range(nb):
+        a = At[i].float().numpy().astype(np.float64).T
+        b = Bt[i].float().numpy().astype(np.float64).T
+        _check(C[i].cpu().numpy().T, a @ b, 2.0 ** -20 * (np.abs(a) @ np.abs(b)))
+
+
+def test_gemm_bf16_output_accumulate_alpha():
+    M, N, K = 130, 70, 40
+    g = torch.Generator().manual_seed(9)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(K, N, generator=g).to(torch.bfloat16)
+    C0 = torch.randn(M, N, generator=g).to(torch.bfloat16)
+    C = C0.cuda()
+    _gemm(M, N, K, 1, A.cuda(), (K, 1, 0), B.cuda(), (N, 1, 0), C, (N, 1, 0), out_bf16=1, alpha=0.5, beta=1)
+    a, b = A.float().numpy().astype(np.float64), B.float().numpy().astype(np.float64)
+    ref = C0.float().numpy() + 0.5 * (a @ b)
+    got = C.float().cpu().numpy()
+    # result rounded to BF16 once: half an ulp of 2^-8 relative, plus the accumulation bound
+    _check(got, ref, 2.0 ** -8 * np.abs(ref) + 2.0 ** -20 * (np.abs(a) @ np.abs(b)))
