@@ -230,6 +230,36 @@ LBM_API lbm_status lbm_gemm_bf16(int M, int N, int K, int batch, const void* A, 
                                  long long scm, long long scn, long long scb, int out_bf16, float alpha, int beta,
                                  unsigned int* err, void* stream);
 
+/* 3D Fourier neural operator (FNO), predicting steady fields from inputs on a D^3 grid:
+ *   h0 = P a + p;  h_{l+1} = act(K_l h_l + W_l h_l + b_l), act = GELU (identity on the last layer);
+ *   out = Q h_L + q,
+ * where K_l is the truncated spectral convolution: forward DFT over (z, y, x) without scaling,
+ * modes |kz|, |ky| < m (both signs) and 0 <= kx < m, a learned complex width x width matrix per
+ * mode, inverse DFT scaled by 1/D^3 taking the real part with kx > 0 counted twice (the inverse
+ * of a real-to-complex transform).  Transforms and 1x1 maps run on lbm_gemm_bf16 (BF16 operands,
+ * FP32 accumulation); parameters, gradients and Adam state are FP32.
+ * Parameter vector (FP32): P[W][Ci], p[W], then per layer Wm[m][2m][2m][W][W][2] (kx, ky, kz,
+ * out channel, in channel, re/im; ky and kz index the kept modes 0..m-1 then D-m..D-1),
+ * Wc[W][W] (out, in), b[W]; then Q[Co][W], q[Co].  Tensors are [batch][channel][z][y][x] FP32. */
+typedef struct lbm_no lbm_no;
+/* D >= 4, 2 m <= D, W, L, Ci, Co, max_batch >= 1; parameters drawn from seed. */
+LBM_API lbm_status lbm_no_create(int D, int width, int modes, int layers, int in_ch, int out_ch, int max_batch,
+                                 unsigned long long seed, void* stream, lbm_no** out);
+LBM_API long long lbm_no_param_count(const lbm_no* n);
+/* Copies the parameter vector out of (set = 0) or into (set = 1) the model; host or device. */
+LBM_API lbm_status lbm_no_params(lbm_no* n, float* params, int set);
+/* Copies the gradient vector of the last lbm_no_backward / lbm_no_train_step; host or device. */
+LBM_API lbm_status lbm_no_grads(lbm_no* n, float* grads);
+/* out = model(in) for batch samples (device or host pointers); keeps the activations. */
+LBM_API lbm_status lbm_no_forward(lbm_no* n, int batch, const float* in, float* out);
+/* Gradient of sum(dout * out) of the last forward with respect to every parameter. */
+LBM_API lbm_status lbm_no_backward(lbm_no* n, const float* dout);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error over all outputs;
+ * loss (optional, host) receives the loss before the step.  in, target: device pointers. */
+LBM_API lbm_status lbm_no_train_step(lbm_no* n, int batch, const float* in, const float* target, float lr, double* loss);
+LBM_API const char* lbm_no_last_error(const lbm_no* n);
+LBM_API void lbm_no_destroy(lbm_no* n);
+
 /* Allocation-free FP64 diagnostics (the paper has no counterpart; this is a library service).
  * For callers that must not allocate device memory on their hot path -- a framework whose
  * caching allocator owns the device's memory budget, or a loop that cannot afford the implicit

@@ -126,6 +126,24 @@ def lib():
                                     _P, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong,
                                     ctypes.c_int, ctypes.c_float, ctypes.c_int, _P, _P]
         L.lbm_gemm_bf16.restype = st
+        L.lbm_no_create.argtypes = [ctypes.c_int] * 7 + [ctypes.c_ulonglong, _P, ctypes.POINTER(_P)]
+        L.lbm_no_create.restype = st
+        L.lbm_no_param_count.argtypes = [_P]
+        L.lbm_no_param_count.restype = ctypes.c_longlong
+        L.lbm_no_params.argtypes = [_P, _P, ctypes.c_int]
+        L.lbm_no_params.restype = st
+        L.lbm_no_grads.argtypes = [_P, _P]
+        L.lbm_no_grads.restype = st
+        L.lbm_no_forward.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.lbm_no_forward.restype = st
+        L.lbm_no_backward.argtypes = [_P, _P]
+        L.lbm_no_backward.restype = st
+        L.lbm_no_train_step.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+        L.lbm_no_train_step.restype = st
+        L.lbm_no_last_error.argtypes = [_P]
+        L.lbm_no_last_error.restype = ctypes.c_char_p
+        L.lbm_no_destroy.argtypes = [_P]
+        L.lbm_no_destroy.restype = None
         L.lbm_time.argtypes = [_P]
         L.lbm_time.restype = ctypes.c_longlong
         L.lbm_last_error.argtypes = [_P]

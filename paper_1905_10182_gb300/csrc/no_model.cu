@@ -1,0 +1,799 @@
+// Neural operator for the warm start of steady solves: a 3D Fourier neural operator
+//   h0 = P a + p;  h_{l+1} = act(K_l h_l + W_l h_l + b_l) (act = GELU, identity on the last layer);
+//   out = Q h_L + q,
+// with K_l the truncated spectral convolution: rfft over (z, y, x), keep the modes
+// |kz|, |ky| < m (both signs) and 0 <= kx < m, multiply each mode by a learned complex W x W
+// matrix, inverse transform (normalised by 1/D^3, real part, kx > 0 counted twice).
+// The transforms are real GEMMs against constant DFT matrices (complex numbers as 2 x 2 real
+// blocks) on the tcgen05 BF16 GEMM, as are the 1x1 convolutions and every adjoint in the
+// backward pass; activations feeding a GEMM are BF16, accumulation and stored state FP32.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cmlbm.h"
+#include "no_gemm.h"
+
+using namespace cmlbm;
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+// ------------------------------------------------------------------------------ elementwise kernels
+__global__ void k_f32_to_bf16(const float* __restrict__ x, bf16* __restrict__ y, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16(x[i]);
+}
+
+// out[b][c][s] = sum_i P[c][i] a[b][i][s] + p[c]  (FP32 and BF16 copies)
+__global__ void k_lift(const float* __restrict__ a, const float* __restrict__ P, const float* __restrict__ p, int B, int Ci,
+                       int W, long long S, float* __restrict__ h, bf16* __restrict__ hb) {
+    const long long total = (long long)B * W * S;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long s = idx % S;
+        const int c = (int)((idx / S) % W);
+        const int b = (int)(idx / (S * W));
+        float v = p[c];
+        for (int i = 0; i < Ci; ++i) v += P[c * Ci + i] * a[((long long)b * Ci + i) * S + s];
+        h[idx] = v;
+        hb[idx] = __float2bfloat16(v);
+    }
+}
+
+// out[b][o][s] = sum_c Q[o][c] h[b][c][s] + q[o]
+__global__ void k_project(const float* __restrict__ h, const float* __restrict__ Q, const float* __restrict__ q, int B, int W,
+                          int Co, long long S, float* __restrict__ out) {
+    const long long total = (long long)B * Co * S;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long s = idx % S;
+        const int o = (int)((idx / S) % Co);
+        const int b = (int)(idx / (S * Co));
+        float v = q[o];
+        for (int c = 0; c < W; ++c) v += Q[o * W + c] * h[((long long)b * W + c) * S + s];
+        out[idx] = v;
+    }
+}
+
+// dh[b][c][s] = sum_o Q[o][c] dout[b][o][s]
+__global__ void k_project_bwd_x(const float* __restrict__ dout, const float* __restrict__ Q, int B, int W, int Co, long long S,
+                                float* __restrict__ dh) {
+    const long long total = (long long)B * W * S;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long s = idx % S;
+        const int c = (int)((idx / S) % W);
+        const int b = (int)(idx / (S * W));
+        float v = 0.0f;
+        for (int o = 0; o < Co; ++o) v += Q[o * W + c] * dout[((long long)b * Co + o) * S + s];
+        dh[idx] = v;
+    }
+}
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+    const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
+    const float pdf = 0.39894228040143268f * expf(-0.5f * x * x);
+    return cdf + x * pdf;
+}
+
+// z[b][o][s] += bias[o]; h = act(z) (BF16 copy for the next GEMMs)
+__global__ void k_bias_act(float* __restrict__ z, const float* __restrict__ bias, int W, long long S, long long total,
+                           int use_gelu, bf16* __restrict__ hb) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int o = (int)((idx / S) % W);
+        const float v = z[idx] + bias[o];
+        z[idx] = v;
+        hb[idx] = __float2bfloat16(use_gelu ? gelu(v) : v);
+    }
+}
+
+// dz = dh * act'(z); BF16 copy for the GEMMs
+__global__ void k_act_bwd(const float* __restrict__ dh, const float* __restrict__ z, long long total, int use_gelu,
+                          float* __restrict__ dz, bf16* __restrict__ dzb) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const float v = use_gelu ? dh[idx] * gelu_grad(z[idx]) : dh[idx];
+        dz[idx] = v;
+        dzb[idx] = __float2bfloat16(v);
+    }
+}
+
+// Generic 6-axis permutation of a BF16 tensor: out axis j is in axis perm[j].
+struct Perm6 {
+    long long din[6];
+    int perm[6];
+};
+__global__ void k_permute6(const bf16* __restrict__ in, bf16* __restrict__ out, Perm6 P, long long total) {
+    long long sin[6];
+    sin[5] = 1;
+    for (int a = 4; a >= 0; --a) sin[a] = sin[a + 1] * P.din[a + 1];
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long rem = idx, off = 0;
+        for (int j = 5; j >= 0; --j) {
+            const long long dj = P.din[P.perm[j]];
+            const long long ij = rem % dj;
+            rem /= dj;
+            off += ij * sin[P.perm[j]];
+        }
+        out[idx] = in[off];
+    }
+}
+
+// Mode mixing.  X[b][c][kx][ky][ri][kz] (FP32), W[kx][ky][kz][o][c][ri], Y[b][o][kx][ky][ri][kz] (BF16).
+struct MixDims {
+    int B, W, MX, MY, MZ;
+};
+__device__ __forceinline__ long long xidx(const MixDims& d, int b, int c, int kx, int ky, int ri, int kz) {
+    return ((((long long)(b * d.W + c) * d.MX + kx) * d.MY + ky) * 2 + ri) * d.MZ + kz;
+}
+__device__ __forceinline__ long long widx(const MixDims& d, int kx, int ky, int kz, int o, int c) {
+    return (((((long long)kx * d.MY + ky) * d.MZ + kz) * d.W + o) * d.W + c) * 2;
+}
+__global__ void k_mix_fwd(const float* __restrict__ X, const float* __restrict__ Wm, MixDims d, bf16* __restrict__ Y) {
+    const long long modes = (long long)d.MX * d.MY * d.MZ;
+    const long long total = (long long)d.B * d.W * modes;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int kz = (int)(idx % d.MZ);
+        const int ky = (int)((idx / d.MZ) % d.MY);
+        const int kx = (int)((idx / ((long long)d.MZ * d.MY)) % d.MX);
+        const int o = (int)((idx / modes) % d.W);
+        const int b = (int)(idx / (modes * d.W));
+        float yr = 0.0f, yi = 0.0f;
+        for (int c = 0; c < d.W; ++c) {
+            const float xr = X[xidx(d, b, c, kx, ky, 0, kz)], xi = X[xidx(d, b, c, kx, ky, 1, kz)];
+            const long long w = widx(d, kx, ky, kz, o, c);
+            const float wr = Wm[w], wi = Wm[w + 1];
+            yr += wr * xr - wi * xi;
+            yi += wr * xi + wi * xr;
+        }
+        Y[xidx(d, b, o, kx, ky, 0, kz)] = __float2bfloat16(yr);
+        Y[xidx(d, b, o, kx, ky, 1, kz)] = __float2bfloat16(yi);
+    }
+}
+// dX (BF16) from dY (FP32)
+__global__ void k_mix_bwd_x(const float* __restrict__ dY, const float* __restrict__ Wm, MixDims d, bf16* __restrict__ dX) {
+    const long long modes = (long long)d.MX * d.MY * d.MZ;
+    const long long total = (long long)d.B * d.W * modes;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int kz = (int)(idx % d.MZ);
+        const int ky = (int)((idx / d.MZ) % d.MY);
+        const int kx = (int)((idx / ((long long)d.MZ * d.MY)) % d.MX);
+        const int c = (int)((idx / modes) % d.W);
+        const int b = (int)(idx / (modes * d.W));
+        float xr = 0.0f, xi = 0.0f;
+        for (int o = 0; o < d.W; ++o) {
+            const float yr = dY[xidx(d, b, o, kx, ky, 0, kz)], yi = dY[xidx(d, b, o, kx, ky, 1, kz)];
+            const long long w = widx(d, kx, ky, kz, o, c);
+            const float wr = Wm[w], wi = Wm[w + 1];
+            xr += wr * yr + wi * yi;
+            xi += -wi * yr + wr * yi;
+        }
+        dX[xidx(d, b, c, kx, ky, 0, kz)] = __float2bfloat16(xr);
+        dX[xidx(d, b, c, kx, ky, 1, kz)] = __float2bfloat16(xi);
+    }
+}
+// dW += sum_b (per mode, o, c)
+__global__ void k_mix_bwd_w(const float* __restrict__ dY, const float* __restrict__ X, MixDims d, float* __restrict__ dW) {
+    const long long modes = (long long)d.MX * d.MY * d.MZ;
+    const long long total = modes * d.W * d.W;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % d.W);
+        const int o = (int)((idx / d.W) % d.W);
+        const long long m = idx / ((long long)d.W * d.W);
+        const int kz = (int)(m % d.MZ);
+        const int ky = (int)((m / d.MZ) % d.MY);
+        const int kx = (int)(m / ((long long)d.MZ * d.MY));
+        float gr = 0.0f, gi = 0.0f;
+        for (int b = 0; b < d.B; ++b) {
+            const float yr = dY[xidx(d, b, o, kx, ky, 0, kz)], yi = dY[xidx(d, b, o, kx, ky, 1, kz)];
+            const float xr = X[xidx(d, b, c, kx, ky, 0, kz)], xi = X[xidx(d, b, c, kx, ky, 1, kz)];
+            gr += yr * xr + yi * xi;
+            gi += -yr * xi + yi * xr;
+        }
+        const long long w = widx(d, kx, ky, kz, o, c);
+        dW[w] += gr;
+        dW[w + 1] += gi;
+    }
+}
+
+// out[i][j] += sum_{b,s} X[b][i][s] * (Y ? Y[b][j][s] : 1); one block per (i, j, chunk of the (b, s) range)
+__global__ void k_reduce_bs(const float* __restrict__ X, const float* __restrict__ Y, int B, int Cx, int Cy, long long S,
+                            int chunks, float* __restrict__ out) {
+    const int pair = blockIdx.x / chunks, chunk = blockIdx.x % chunks;
+    const int i = pair / Cy, j = pair % Cy;
+    const long long n = (long long)B * S;
+    const long long per = (n + chunks - 1) / chunks;
+    const long long lo = chunk * per, hi = (lo + per < n) ? lo + per : n;
+    double acc = 0.0;
+    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+        const long long b = t / S, s = t % S;
+        const float x = X[(b * Cx + i) * S + s];
+        acc += Y ? (double)x * Y[(b * Cy + j) * S + s] : (double)x;
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&out[i * Cy + j], (float)sh[0]);
+}
+
+// sum of partial blocks: out[k] += sum_p part[p][k]
+__global__ void k_sum_partials(const float* __restrict__ part, int P, int K, float* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    float a = 0.0f;
+    for (int p = 0; p < P; ++p) a += part[(long long)p * K + k];
+    out[k] += a;
+}
+
+// mean squared error over all elements; dout = 2 (out - t) / n; loss accumulated in FP64
+__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t, long long n, float* __restrict__ dout,
+                      double* __restrict__ loss) {
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float e = out[i] - t[i];
+        dout[i] = 2.0f * e / (float)n;
+        acc += (double)e * e;
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, sh[0] / (double)n);
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v, long long n,
+                       float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+inline unsigned grid_for(long long n, int threads = 256) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 152LL * 32) b = 152LL * 32;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+uint64_t splitmix(uint64_t& s) {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double unif(uint64_t& s) { return (double)(splitmix(s) >> 11) * (1.0 / 9007199254740992.0); }
+
+}  // namespace
+
+struct lbm_no {
+    int D = 0, W = 0, modes = 0, L = 0, Ci = 0, Co = 0, maxB = 0;
+    int MX = 0, MY = 0, MZ = 0;
+    long long S = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // parameter offsets into the flat FP32 vector
+    long long oP = 0, op = 0, oQ = 0, oq = 0, nparam = 0;
+    std::vector<long long> oWm, oWc, obc;
+    float* params = nullptr;
+    float* grads = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    long long adam_t = 0;
+    bf16* wcb = nullptr;  // BF16 copies of the 1x1 weights, L x W x W
+    // DFT matrices (BF16)
+    bf16 *FX = nullptr, *GY = nullptr, *GZ = nullptr, *HZ = nullptr, *HY = nullptr, *HX = nullptr;
+    // activations for the last forward
+    int B = 0;
+    float* a_in = nullptr;               // lift input copy [B][Ci][S]
+    std::vector<bf16*> hb;               // L + 1 BF16 layer inputs [B][W][S]
+    std::vector<float*> z;               // L pre-activations [B][W][S] (z[L-1] is h_L)
+    std::vector<float*> Xh;              // L mode coefficients [B][W][MX][MY][2][MZ]
+    float* h0 = nullptr;                 // FP32 lift output
+    // work buffers
+    bf16 *t1 = nullptr, *t2 = nullptr, *t2p = nullptr, *yh = nullptr, *u1 = nullptr, *u1p = nullptr, *u2 = nullptr;
+    float* dyh = nullptr;
+    float *dh = nullptr, *dh2 = nullptr, *dz = nullptr;
+    bf16* dzb = nullptr;
+    float* part = nullptr;  // split-K partials of the 1x1 weight gradient
+    float* dout = nullptr;
+    double* loss_d = nullptr;
+    unsigned int* gemm_err = nullptr;
+};
+
+namespace {
+
+lbm_status nfail(lbm_no* n, lbm_status s, const std::string& m) {
+    if (n) n->err = m;
+    return s;
+}
+lbm_status ncuda(lbm_no* n, cudaError_t e, const char* what) {
+    cudaGetLastError();
+    return nfail(n, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define NCK(n, call, what)                                  \
+    do {                                                    \
+        cudaError_t _e = (call);                            \
+        if (_e != cudaSuccess) return ncuda((n), _e, what); \
+    } while (0)
+
+constexpr int KSPLIT = 8192;  // K chunk of the split-K 1x1 weight gradient
+
+cudaError_t gemm(lbm_no* n, int M, int N, int K, int batch, const bf16* A, long long sam, long long sak, long long sab,
+                 const bf16* Bm, long long sbk, long long sbn, long long sbb, void* C, long long scm, long long scn,
+                 long long scb, int out_bf16, int beta) {
+    GemmArgs g;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.A = A;
+    g.sam = sam;
+    g.sak = sak;
+    g.sab = sab;
+    g.B = Bm;
+    g.sbk = sbk;
+    g.sbn = sbn;
+    g.sbb = sbb;
+    g.C = C;
+    g.scm = scm;
+    g.scn = scn;
+    g.scb = scb;
+    g.out_bf16 = out_bf16;
+    g.alpha = 1.0f;
+    g.beta = beta;
+    g.err = n->gemm_err;
+    return launch_gemm_bf16(g, batch, n->stream);
+}
+
+cudaError_t permute(lbm_no* n, const bf16* in, bf16* out, const long long din[6], const int perm[6]) {
+    Perm6 P;
+    long long total = 1;
+    for (int a = 0; a < 6; ++a) {
+        P.din[a] = din[a];
+        P.perm[a] = perm[a];
+        total *= din[a];
+    }
+    k_permute6<<<grid_for(total), 256, 0, n->stream>>>(in, out, P, total);
+    return cudaGetLastError();
+}
+
+// wave number of kept index k (0 .. 2m-1) along an axis of D points: 0..m-1, then D-m..D-1
+int wave(int k, int m, int D) { return k < m ? k : D - 2 * m + k; }
+
+lbm_status upload_dft(lbm_no* n) {
+    const int D = n->D, MX = n->MX, MY = n->MY, MZ = n->MZ;
+    const double tw = 2.0 * M_PI / D;
+    auto up = [&](bf16** dst, const std::vector<float>& h) -> lbm_status {
+        std::vector<bf16> b(h.size());
+        for (size_t i = 0; i < h.size(); ++i) b[i] = __float2bfloat16(h[i]);
+        NCK(n, cudaMalloc(dst, sizeof(bf16) * b.size()), "cudaMalloc(dft)");
+        NCK(n, cudaMemcpy(*dst, b.data(), sizeof(bf16) * b.size(), cudaMemcpyHostToDevice), "dft upload");
+        return LBM_OK;
+    };
+    // FX [x][(kx, ri)]: e^{-i 2 pi kx x / D}
+    std::vector<float> fx((size_t)D * 2 * MX);
+    for (int x = 0; x < D; ++x)
+        for (int k = 0; k < MX; ++k) {
+            fx[(size_t)x * 2 * MX + 2 * k] = (float)cos(tw * k * x);
+            fx[(size_t)x * 2 * MX + 2 * k + 1] = (float)-sin(tw * k * x);
+        }
+    // G [(ri_in, y)][(ri_out, k)]: multiplication by e^{-i theta}
+    auto fwd_complex = [&](int Mk) {
+        std::vector<float> g((size_t)2 * D * 2 * Mk);
+        for (int y = 0; y < D; ++y)
+            for (int k = 0; k < Mk; ++k) {
+                const double th = tw * wave(k, n->modes, D) * y;
+                const double c = cos(th), s = sin(th);
+                g[(size_t)(0 * D + y) * 2 * Mk + 0 * Mk + k] = (float)c;
+                g[(size_t)(1 * D + y) * 2 * Mk + 0 * Mk + k] = (float)s;
+                g[(size_t)(0 * D + y) * 2 * Mk + 1 * Mk + k] = (float)-s;
+                g[(size_t)(1 * D + y) * 2 * Mk + 1 * Mk + k] = (float)c;
+            }
+        return g;
+    };
+    // H [(ri_in, k)][(ri_out, y)]: multiplication by e^{+i theta}
+    auto inv_complex = [&](int Mk) {
+        std::vector<float> h((size_t)2 * Mk * 2 * D);
+        for (int k = 0; k < Mk; ++k)
+            for (int y = 0; y < D; ++y) {
+                const double th = tw * wave(k, n->modes, D) * y;
+                const double c = cos(th), s = sin(th);
+                h[(size_t)(0 * Mk + k) * 2 * D + 0 * D + y] = (float)c;
+                h[(size_t)(1 * Mk + k) * 2 * D + 0 * D + y] = (float)-s;
+                h[(size_t)(0 * Mk + k) * 2 * D + 1 * D + y] = (float)s;
+                h[(size_t)(1 * Mk + k) * 2 * D + 1 * D + y] = (float)c;
+            }
+        return h;
+    };
+    // HX [(kx, ri)][x]: real part of the inverse, 1/D^3, kx > 0 counted twice
+    std::vector<float> hx((size_t)2 * MX * D);
+    const double norm = 1.0 / ((double)D * D * D);
+    for (int k = 0; k < MX; ++k)
+        for (int x = 0; x < D; ++x) {
+            const double cf = (k == 0 ? 1.0 : 2.0) * norm;
+            hx[(size_t)(2 * k) * D + x] = (float)(cf * cos(tw * k * x));
+            hx[(size_t)(2 * k + 1) * D + x] = (float)(-cf * sin(tw * k * x));
+        }
+    lbm_status st;
+    if ((st = up(&n->FX, fx))) return st;
+    if ((st = up(&n->GY, fwd_complex(MY)))) return st;
+    if ((st = up(&n->GZ, fwd_complex(MZ)))) return st;
+    if ((st = up(&n->HZ, inv_complex(MZ)))) return st;
+    if ((st = up(&n->HY, inv_complex(MY)))) return st;
+    if ((st = up(&n->HX, hx))) return st;
+    return LBM_OK;
+}
+
+// spectral convolution of layer l: input hb (BF16 [B][W][S]) -> out (FP32 [B][W][S], overwritten);
+// keeps the mode coefficients in Xh[l] for the weight gradient
+lbm_status spectral_fwd(lbm_no* n, int l, const bf16* hb, float* out) {
+    const int B = n->B, W = n->W, D = n->D, MX = n->MX, MY = n->MY, MZ = n->MZ;
+    const long long D2 = (long long)D * D;
+    const long long BWD = (long long)B * W * D;
+    // x: [bcz][y][x] x FX -> t1 [bcz][(kx,ri)][y]
+    NCK(n, gemm(n, D, 2 * MX, D, (int)BWD, hb, D, 1, D2, n->FX, 2 * MX, 1, 0, n->t1, 1, D, 2LL * MX * D, 1, 0), "fx");
+    // y: rows (bcz,kx), K = (ri,y) -> t2 [b][c][z][kx][ri][ky]
+    NCK(n, gemm(n, (int)(BWD * MX), 2 * MY, 2 * D, 1, n->t1, 2 * D, 1, 0, n->GY, 2 * MY, 1, 0, n->t2, 2 * MY, 1, 0, 1, 0), "fy");
+    {
+        const long long din[6] = {B, W, D, MX, 2, MY};
+        const int perm[6] = {0, 1, 3, 5, 4, 2};  // -> [b][c][kx][ky][ri][z]
+        NCK(n, permute(n, n->t2, n->t2p, din, perm), "permute t2");
+    }
+    // z: rows (b,c,kx,ky), K = (ri,z) -> Xh [b][c][kx][ky][ri][kz] FP32
+    const long long R = (long long)B * W * MX * MY;
+    NCK(n, gemm(n, (int)R, 2 * MZ, 2 * D, 1, n->t2p, 2 * D, 1, 0, n->GZ, 2 * MZ, 1, 0, n->Xh[l], 2 * MZ, 1, 0, 0, 0), "fz");
+    MixDims md{B, W, MX, MY, MZ};
+    k_mix_fwd<<<grid_for((long long)B * W * MX * MY * MZ), 256, 0, n->stream>>>(n->Xh[l], n->params + n->oWm[l], md, n->yh);
+    NCK(n, cudaGetLastError(), "mix");
+    // inverse z: rows (b,o,kx,ky), K = (ri,kz) -> u1 [b][o][kx][ky][ri][z]
+    NCK(n, gemm(n, (int)R, 2 * D, 2 * MZ, 1, n->yh, 2 * MZ, 1, 0, n->HZ, 2 * D, 1, 0, n->u1, 2 * D, 1, 0, 1, 0), "iz");
+    {
+        const long long din[6] = {B, W, MX, MY, 2, D};
+        const int perm[6] = {0, 1, 5, 2, 4, 3};  // -> [b][o][z][kx][ri][ky]
+        NCK(n, permute(n, n->u1, n->u1p, din, perm), "permute u1");
+    }
+    // inverse y: rows (b,o,z,kx), K = (ri,ky) -> u2 [b][o][z][kx][ri][y]
+    NCK(n, gemm(n, (int)(BWD * MX), 2 * D, 2 * MY, 1, n->u1p, 2 * MY, 1, 0, n->HY, 2 * D, 1, 0, n->u2, 2 * D, 1, 0, 1, 0), "iy");
+    // inverse x: per (b,o,z): [y][(kx,ri)] x HX -> out [y][x]
+    NCK(n, gemm(n, D, D, 2 * MX, (int)BWD, n->u2, 1, D, 2LL * MX * D, n->HX, D, 1, 0, out, D, 1, D2, 0, 0), "ix");
+    return LBM_OK;
+}
+
+// adjoint of the spectral convolution of layer l: dzb (BF16 gradient of its output) -> dh
+// (FP32, accumulated); adds the mixing-weight gradient
+lbm_status spectral_bwd(lbm_no* n, int l, const bf16* dzb, float* dh) {
+    const int B = n->B, W = n->W, D = n->D, MX = n->MX, MY = n->MY, MZ = n->MZ;
+    const long long D2 = (long long)D * D;
+    const long long BWD = (long long)B * W * D;
+    const long long R = (long long)B * W * MX * MY;
+    // adjoint of inverse x -> u2 layout
+    NCK(n, gemm(n, D, 2 * MX, D, (int)BWD, dzb, D, 1, D2, n->HX, 1, D, 0, n->u2, 1, D, 2LL * MX * D, 1, 0), "ix^T");
+    // adjoint of inverse y -> u1p layout
+    NCK(n, gemm(n, (int)(BWD * MX), 2 * MY, 2 * D, 1, n->u2, 2 * D, 1, 0, n->HY, 1, 2 * D, 0, n->u1p, 2 * MY, 1, 0, 1, 0),
+        "iy^T");
+    {
+        const long long din[6] = {B, W, D, MX, 2, MY};
+        const int perm[6] = {0, 1, 3, 5, 4, 2};  // [b][o][z][kx][ri][ky] -> [b][o][kx][ky][ri][z]
+        NCK(n, permute(n, n->u1p, n->u1, din, perm), "permute u1^T");
+    }
+    // adjoint of inverse z -> dYh (FP32)
+    NCK(n, gemm(n, (int)R, 2 * MZ, 2 * D, 1, n->u1, 2 * D, 1, 0, n->HZ, 1, 2 * D, 0, n->dyh, 2 * MZ, 1, 0, 0, 0), "iz^T");
+    MixDims md{B, W, MX, MY, MZ};
+    k_mix_bwd_w<<<grid_for((long long)MX * MY * MZ * W * W), 256, 0, n->stream>>>(n->dyh, n->Xh[l], md,
+                                                                                   n->grads + n->oWm[l]);
+    NCK(n, cudaGetLastError(), "mix dW");
+    k_mix_bwd_x<<<grid_for((long long)B * W * MX * MY * MZ), 256, 0, n->stream>>>(n->dyh, n->params + n->oWm[l], md, n->yh);
+    NCK(n, cudaGetLastError(), "mix dX");
+    // adjoint of forward z -> t2p layout
+    NCK(n, gemm(n, (int)R, 2 * D, 2 * MZ, 1, n->yh, 2 * MZ, 1, 0, n->GZ, 1, 2 * MZ, 0, n->t2p, 2 * D, 1, 0, 1, 0), "fz^T");
+    {
+        const long long din[6] = {B, W, MX, MY, 2, D};
+        const int perm[6] = {0, 1, 5, 2, 4, 3};  // [b][c][kx][ky][ri][z] -> [b][c][z][kx][ri][ky]
+        NCK(n, permute(n, n->t2p, n->t2, din, perm), "permute t2^T");
+    }
+    // adjoint of forward y -> t1 layout
+    NCK(n, gemm(n, (int)(BWD * MX), 2 * D, 2 * MY, 1, n->t2, 2 * MY, 1, 0, n->GY, 1, 2 * MY, 0, n->t1, 2 * D, 1, 0, 1, 0),
+        "fy^T");
+    // adjoint of forward x -> dh [bcz][y][x] (accumulate)
+    NCK(n, gemm(n, D, D, 2 * MX, (int)BWD, n->t1, 1, D, 2LL * MX * D, n->FX, 1, 2 * MX, 0, dh, D, 1, D2, 0, 1), "fx^T");
+    return LBM_OK;
+}
+
+lbm_status ensure_batch(lbm_no* n, int B) {
+    if (B < 1 || B > n->maxB) return nfail(n, LBM_ERR_ARG, "batch must be in [1, max_batch]");
+    n->B = B;
+    return LBM_OK;
+}
+
+lbm_status forward(lbm_no* n, int B, const float* in, float* out) {
+    lbm_status st = ensure_batch(n, B);
+    if (st) return st;
+    const int W = n->W;
+    const long long S = n->S, tot = (long long)B * W * S;
+    NCK(n, cudaMemcpyAsync(n->a_in, in, sizeof(float) * B * n->Ci * S, cudaMemcpyDefault, n->stream), "input copy");
+    k_lift<<<grid_for(tot), 256, 0, n->stream>>>(n->a_in, n->params + n->oP, n->params + n->op, B, n->Ci, W, S, n->h0,
+                                                n->hb[0]);
+    NCK(n, cudaGetLastError(), "lift");
+    for (int l = 0; l < n->L; ++l) {
+        k_f32_to_bf16<<<grid_for((long long)W * W), 256, 0, n->stream>>>(n->params + n->oWc[l], n->wcb + (long long)l * W * W,
+                                                                           (long long)W * W);
+        st = spectral_fwd(n, l, n->hb[l], n->z[l]);
+        if (st) return st;
+        // 1x1 conv accumulated onto the spectral output: z[b][o][s] += sum_c Wc[o][c] h[b][c][s]
+        NCK(n, gemm(n, (int)S, W, W, B, n->hb[l], 1, S, (long long)W * S, n->wcb + (long long)l * W * W, 1, W, 0, n->z[l], 1,
+                    S, (long long)W * S, 0, 1),
+            "conv");
+        k_bias_act<<<grid_for(tot), 256, 0, n->stream>>>(n->z[l], n->params + n->obc[l], W, S, tot, l < n->L - 1 ? 1 : 0,
+                                                        n->hb[l + 1]);
+        NCK(n, cudaGetLastError(), "bias act");
+    }
+    k_project<<<grid_for((long long)B * n->Co * S), 256, 0, n->stream>>>(n->z[n->L - 1], n->params + n->oQ,
+                                                                        n->params + n->oq, B, W, n->Co, S, out);
+    NCK(n, cudaGetLastError(), "project");
+    return LBM_OK;
+}
+
+// gradients of sum(dout * out) for the last forward (overwrites grads)
+lbm_status backward(lbm_no* n, const float* dout) {
+    const int B = n->B, W = n->W, L = n->L;
+    const long long S = n->S, tot = (long long)B * W * S;
+    NCK(n, cudaMemsetAsync(n->grads, 0, sizeof(float) * n->nparam, n->stream), "zero grads");
+    const int chunks = 64;
+    // projection
+    k_reduce_bs<<<n->Co * W * chunks, 256, 0, n->stream>>>(dout, n->z[L - 1], B, n->Co, W, S, chunks, n->grads + n->oQ);
+    k_reduce_bs<<<n->Co * chunks, 256, 0, n->stream>>>(dout, nullptr, B, n->Co, 1, S, chunks, n->grads + n->oq);
+    k_project_bwd_x<<<grid_for(tot), 256, 0, n->stream>>>(dout, n->params + n->oQ, B, W, n->Co, S, n->dh);
+    NCK(n, cudaGetLastError(), "project bwd");
+    for (int l = L - 1; l >= 0; --l) {
+        k_act_bwd<<<grid_for(tot), 256, 0, n->stream>>>(n->dh, n->z[l], tot, l < L - 1 ? 1 : 0, n->dz, n->dzb);
+        k_reduce_bs<<<W * chunks, 256, 0, n->stream>>>(n->dz, nullptr, B, W, 1, S, chunks, n->grads + n->obc[l]);
+        NCK(n, cudaGetLastError(), "act bwd");
+        // 1x1 weight gradient: dWc[o][c] = sum_{b,s} dz[b][o][s] h[b][c][s], split-K over s: chunks
+        // of KSPLIT as one batched GEMM per sample, the remainder as one more
+        const long long kc = S < KSPLIT ? S : KSPLIT;
+        const int full = (int)(S / kc);
+        const long long rest = S - (long long)full * kc;
+        const int nk = full + (rest > 0 ? 1 : 0);
+        for (int b = 0; b < B; ++b) {
+            const bf16* dz_b = n->dzb + (long long)b * W * S;
+            const bf16* h_b = n->hb[l] + (long long)b * W * S;
+            float* part_b = n->part + (long long)b * nk * W * W;
+            NCK(n, gemm(n, W, W, (int)kc, full, dz_b, S, 1, kc, h_b, 1, S, kc, part_b, W, 1, (long long)W * W, 0, 0),
+                "conv dW");
+            if (rest > 0)
+                NCK(n, gemm(n, W, W, (int)rest, 1, dz_b + full * kc, S, 1, 0, h_b + full * kc, 1, S, 0,
+                            part_b + (long long)full * W * W, W, 1, 0, 0, 0),
+                    "conv dW rest");
+        }
+        k_sum_partials<<<(W * W + 255) / 256, 256, 0, n->stream>>>(n->part, B * nk, W * W, n->grads + n->oWc[l]);
+        NCK(n, cudaGetLastError(), "conv dW sum");
+        // dh_l = Wc^T dz (conv) + spectral adjoint
+        NCK(n, gemm(n, (int)S, W, W, B, n->dzb, 1, S, (long long)W * S, n->wcb + (long long)l * W * W, W, 1, 0, n->dh2, 1, S,
+                    (long long)W * S, 0, 0),
+            "conv dX");
+        lbm_status st = spectral_bwd(n, l, n->dzb, n->dh2);
+        if (st) return st;
+        std::swap(n->dh, n->dh2);
+    }
+    // lift
+    k_reduce_bs<<<W * n->Ci * chunks, 256, 0, n->stream>>>(n->dh, n->a_in, B, W, n->Ci, S, chunks, n->grads + n->oP);
+    k_reduce_bs<<<W * chunks, 256, 0, n->stream>>>(n->dh, nullptr, B, W, 1, S, chunks, n->grads + n->op);
+    NCK(n, cudaGetLastError(), "lift bwd");
+    return LBM_OK;
+}
+
+lbm_status check_gemm(lbm_no* n) {
+    unsigned int e = 0;
+    NCK(n, cudaMemcpyAsync(&e, n->gemm_err, sizeof(e), cudaMemcpyDeviceToHost, n->stream), "gemm flag");
+    NCK(n, cudaStreamSynchronize(n->stream), "sync");
+    if (e) return nfail(n, LBM_ERR_TIMEOUT, "a tensor-core GEMM wait timed out");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_no_create(int D, int W, int modes, int L, int Ci, int Co, int maxB, unsigned long long seed, void* stream,
+                         lbm_no** out) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (D < 4 || W < 1 || modes < 1 || 2 * modes > D || L < 1 || Ci < 1 || Co < 1 || maxB < 1) return LBM_ERR_ARG;
+    lbm_no* n = new (std::nothrow) lbm_no();
+    if (!n) return LBM_ERR_OOM;
+    auto bail = [&](lbm_status s) {
+        lbm_no_destroy(n);
+        return s;
+    };
+    n->D = D;
+    n->W = W;
+    n->modes = modes;
+    n->L = L;
+    n->Ci = Ci;
+    n->Co = Co;
+    n->maxB = maxB;
+    n->MX = modes;
+    n->MY = 2 * modes;
+    n->MZ = 2 * modes;
+    n->S = (long long)D * D * D;
+    n->stream = static_cast<cudaStream_t>(stream);
+    // parameter layout
+    long long off = 0;
+    n->oP = off;
+    off += (long long)W * Ci;
+    n->op = off;
+    off += W;
+    const long long nm = (long long)n->MX * n->MY * n->MZ;
+    for (int l = 0; l < L; ++l) {
+        n->oWm.push_back(off);
+        off += nm * W * W * 2;
+        n->oWc.push_back(off);
+        off += (long long)W * W;
+        n->obc.push_back(off);
+        off += W;
+    }
+    n->oQ = off;
+    off += (long long)Co * W;
+    n->oq = off;
+    off += Co;
+    n->nparam = off;
+    // initial parameters: uniform(-1/sqrt(fan_in), +) for the dense maps, [0, 1/W^2) for the
+    // mode matrices, zero biases
+    std::vector<float> p(n->nparam, 0.0f);
+    uint64_t s = seed * 0x9E3779B97F4A7C15ull + 12345;
+    auto fill = [&](long long o, long long cnt, double lo, double hi) {
+        for (long long i = 0; i < cnt; ++i) p[o + i] = (float)(lo + (hi - lo) * unif(s));
+    };
+    fill(n->oP, (long long)W * Ci, -1.0 / sqrt(Ci), 1.0 / sqrt(Ci));
+    for (int l = 0; l < L; ++l) {
+        fill(n->oWm[l], nm * W * W * 2, 0.0, 1.0 / ((double)W * W));
+        fill(n->oWc[l], (long long)W * W, -1.0 / sqrt(W), 1.0 / sqrt(W));
+    }
+    fill(n->oQ, (long long)Co * W, -1.0 / sqrt(W), 1.0 / sqrt(W));
+
+    const long long S = n->S, act = (long long)maxB * W * S;
+    const long long rows_y = (long long)maxB * W * D * n->MX;  // rows of the y stages
+    const long long rows_z = (long long)maxB * W * n->MX * n->MY;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+    };
+    alloc((void**)&n->params, sizeof(float) * n->nparam);
+    alloc((void**)&n->grads, sizeof(float) * n->nparam);
+    alloc((void**)&n->adam_m, sizeof(float) * n->nparam);
+    alloc((void**)&n->adam_v, sizeof(float) * n->nparam);
+    alloc((void**)&n->wcb, sizeof(bf16) * L * W * W);
+    alloc((void**)&n->a_in, sizeof(float) * maxB * Ci * S);
+    alloc((void**)&n->h0, sizeof(float) * act);
+    n->hb.assign(L + 1, nullptr);
+    n->z.assign(L, nullptr);
+    n->Xh.assign(L, nullptr);
+    for (int l = 0; l <= L; ++l) alloc((void**)&n->hb[l], sizeof(bf16) * act);
+    for (int l = 0; l < L; ++l) {
+        alloc((void**)&n->z[l], sizeof(float) * act);
+        alloc((void**)&n->Xh[l], sizeof(float) * rows_z * 2 * n->MZ);
+    }
+    alloc((void**)&n->t1, sizeof(bf16) * rows_y * 2 * D);
+    alloc((void**)&n->t2, sizeof(bf16) * rows_y * 2 * n->MY);
+    alloc((void**)&n->t2p, sizeof(bf16) * rows_z * 2 * D);
+    alloc((void**)&n->yh, sizeof(bf16) * rows_z * 2 * n->MZ);
+    alloc((void**)&n->dyh, sizeof(float) * rows_z * 2 * n->MZ);
+    alloc((void**)&n->u1, sizeof(bf16) * rows_z * 2 * D);
+    alloc((void**)&n->u1p, sizeof(bf16) * rows_y * 2 * n->MY);
+    alloc((void**)&n->u2, sizeof(bf16) * rows_y * 2 * D);
+    alloc((void**)&n->dh, sizeof(float) * act);
+    alloc((void**)&n->dh2, sizeof(float) * act);
+    alloc((void**)&n->dz, sizeof(float) * act);
+    alloc((void**)&n->dzb, sizeof(bf16) * act);
+    alloc((void**)&n->part, sizeof(float) * maxB * ((S + KSPLIT - 1) / KSPLIT + 1) * W * W);
+    alloc((void**)&n->dout, sizeof(float) * maxB * Co * S);
+    alloc((void**)&n->loss_d, sizeof(double));
+    alloc((void**)&n->gemm_err, sizeof(unsigned int));
+    if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA);
+    if (upload_dft(n) != LBM_OK) return bail(LBM_ERR_CUDA);
+    e = cudaMemcpy(n->params, p.data(), sizeof(float) * n->nparam, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(n->grads, 0, sizeof(float) * n->nparam);
+    if (e == cudaSuccess) e = cudaMemset(n->adam_m, 0, sizeof(float) * n->nparam);
+    if (e == cudaSuccess) e = cudaMemset(n->adam_v, 0, sizeof(float) * n->nparam);
+    if (e == cudaSuccess) e = cudaMemset(n->gemm_err, 0, sizeof(unsigned int));
+    if (e != cudaSuccess) return bail(LBM_ERR_CUDA);
+    *out = n;
+    return LBM_OK;
+}
+
+long long lbm_no_param_count(const lbm_no* n) { return n ? n->nparam : -1; }
+
+lbm_status lbm_no_params(lbm_no* n, float* p, int set) {
+    if (!n || !p) return LBM_ERR_ARG;
+    const size_t bytes = sizeof(float) * n->nparam;
+    NCK(n, set ? cudaMemcpyAsync(n->params, p, bytes, cudaMemcpyDefault, n->stream)
+               : cudaMemcpyAsync(p, n->params, bytes, cudaMemcpyDefault, n->stream),
+        "params copy");
+    NCK(n, cudaStreamSynchronize(n->stream), "sync");
+    if (set) n->adam_t = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_no_grads(lbm_no* n, float* g) {
+    if (!n || !g) return LBM_ERR_ARG;
+    NCK(n, cudaMemcpyAsync(g, n->grads, sizeof(float) * n->nparam, cudaMemcpyDefault, n->stream), "grads copy");
+    NCK(n, cudaStreamSynchronize(n->stream), "sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_no_forward(lbm_no* n, int batch, const float* in, float* out) {
+    if (!n || !in || !out) return LBM_ERR_ARG;
+    lbm_status st = forward(n, batch, in, out);
+    if (st) return st;
+    return check_gemm(n);
+}
+
+lbm_status lbm_no_backward(lbm_no* n, const float* dout) {
+    if (!n || !dout || n->B == 0) return LBM_ERR_ARG;
+    lbm_status st = backward(n, dout);
+    if (st) return st;
+    return check_gemm(n);
+}
+
+lbm_status lbm_no_train_step(lbm_no* n, int batch, const float* in, const float* target, float lr, double* loss) {
+    if (!n || !in || !target) return LBM_ERR_ARG;
+    float* out = n->dout;  // the prediction is written here, then overwritten by its gradient
+    lbm_status st = forward(n, batch, in, out);
+    if (st) return st;
+    const long long cnt = (long long)batch * n->Co * n->S;
+    NCK(n, cudaMemsetAsync(n->loss_d, 0, sizeof(double), n->stream), "loss reset");
+    k_mse<<<grid_for(cnt), 256, 0, n->stream>>>(out, target, cnt, n->dout, n->loss_d);
+    NCK(n, cudaGetLastError(), "loss");
+    st = backward(n, n->dout);
+    if (st) return st;
+    ++n->adam_t;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)n->adam_t), c2 = 1.0f - powf(b2, (float)n->adam_t);
+    k_adam<<<grid_for(n->nparam), 256, 0, n->stream>>>(n->params, n->grads, n->adam_m, n->adam_v, n->nparam, lr, b1, b2,
+                                                        1e-8f, c1, c2);
+    NCK(n, cudaGetLastError(), "adam");
+    if (loss) NCK(n, cudaMemcpyAsync(loss, n->loss_d, sizeof(double), cudaMemcpyDeviceToHost, n->stream), "loss copy");
+    return check_gemm(n);
+}
+
+const char* lbm_no_last_error(const lbm_no* n) { return n ? n->err.c_str() : ""; }
+
+void lbm_no_destroy(lbm_no* n) {
+    if (!n) return;
+    cudaStreamSynchronize(n->stream);
+    void* bufs[] = {n->params, n->grads, n->adam_m, n->adam_v, n->wcb, n->a_in, n->h0, n->FX, n->GY, n->GZ, n->HZ, n->HY,
+                    n->HX, n->t1, n->t2, n->t2p, n->yh, n->dyh, n->u1, n->u1p, n->u2, n->dh, n->dh2, n->dz, n->dzb,
+                    n->part, n->dout, n->loss_d, n->gemm_err};
+    for (void* b : bufs) cudaFree(b);
+    for (bf16* b : n->hb) cudaFree(b);
+    for (float* b : n->z) cudaFree(b);
+    for (float* b : n->Xh) cudaFree(b);
+    delete n;
+}
+
+}  // extern "C"
