@@ -89,6 +89,10 @@ typedef struct {
     void* store;           /* NULL: the library allocates the population store.  Otherwise a
                               device buffer of lbm_store_bytes(desc) bytes, 256-byte aligned,
                               owned by the caller and kept alive until lbm_destroy.               */
+    int slab_z;            /* 1: this context is one z slab (nz planes) of a larger domain that is
+                              periodic in z across slabs; the store gets one ghost plane below and
+                              one above, filled by lbm_halo_unpack (see there).  No masks and no
+                              Shan-Chen or field forces with slabs.                               */
 } lbm_desc;
 
 /* Bytes of the population store for desc (27 * N * element size); 0 on invalid sizes. */
@@ -125,6 +129,28 @@ LBM_API lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
  * (LBM_ERR_UNSUPPORTED otherwise).  Populations move bit for bit, so a labelled state checks
  * the streaming indices exactly. */
 LBM_API lbm_status lbm_stream_only(lbm_ctx* ctx, int nsteps);
+
+/* ------------------------------------------------------------------------------------------
+ * z-slab decomposition.  Even steps of the AA update touch only a node's own slots, so slabs
+ * exchange nothing; an odd step reads and writes the slots of the neighbour nodes, so across each
+ * slab face it needs the 9 populations with c_z pointing into the slab (before the step) and
+ * returns the 9 it pushed out (after it).  Per odd step, with B = lbm_halo_bytes(ctx) bytes per
+ * device buffer:
+ *   before:  pack(face 0, stage 0) -> rank below;  pack(face 1, stage 0) -> rank above;
+ *            unpack(face 1, stage 0) <- rank above; unpack(face 0, stage 0) <- rank below;
+ *   lbm_step(ctx, 1);
+ *   after:   pack(face 0, stage 1) -> rank below;  pack(face 1, stage 1) -> rank above;
+ *            unpack(face 1, stage 1) <- rank above; unpack(face 0, stage 1) <- rank below.
+ * Face 0 is the bottom (z = 0) side, face 1 the top.  One slab exchanging with itself is the
+ * periodic domain.  The stage-1 unpack keeps every slot whose source lies behind a y wall (it
+ * holds the node's own bounce-back, which nothing across the face pushed).  Read fields
+ * (lbm_macroscopic, lbm_get_populations) at even parity.
+ * ------------------------------------------------------------------------------------------ */
+LBM_API size_t lbm_halo_bytes(const lbm_ctx* ctx);
+LBM_API lbm_status lbm_halo_pack(lbm_ctx* ctx, int face, int stage, void* buf);
+LBM_API lbm_status lbm_halo_unpack(lbm_ctx* ctx, int face, int stage, const void* buf);
+/* Storage parity: 0 after an odd step or a set call (natural order), 1 after an even step. */
+LBM_API int lbm_parity(const lbm_ctx* ctx);
 
 /* Writes rho and u (u includes F/2, Eq. macroscopic) at the current time.  Any output may be
  * NULL; each is N floats, host or device.  Solid nodes get rho0 and 0.  Waits for the stream;

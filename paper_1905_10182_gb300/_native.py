@@ -30,6 +30,7 @@ class LbmDesc(ctypes.Structure):
         ("storage", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("store", ctypes.c_void_p),
+        ("slab_z", ctypes.c_int),
     ]
 
 
@@ -144,6 +145,14 @@ def lib():
         L.lbm_no_last_error.restype = ctypes.c_char_p
         L.lbm_no_destroy.argtypes = [_P]
         L.lbm_no_destroy.restype = None
+        L.lbm_halo_bytes.argtypes = [_P]
+        L.lbm_halo_bytes.restype = ctypes.c_size_t
+        L.lbm_halo_pack.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P]
+        L.lbm_halo_pack.restype = st
+        L.lbm_halo_unpack.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P]
+        L.lbm_halo_unpack.restype = st
+        L.lbm_parity.argtypes = [_P]
+        L.lbm_parity.restype = ctypes.c_int
         L.lbm_time.argtypes = [_P]
         L.lbm_time.restype = ctypes.c_longlong
         L.lbm_last_error.argtypes = [_P]

@@ -18,8 +18,10 @@
 using namespace cmlbm;
 
 struct lbm_ctx {
-    int nx = 0, ny = 0, nz = 0;
-    long long N = 0;
+    int nx = 0, ny = 0, nz = 0;  // nz: planes of the store (the caller's nz + 2 for a z slab)
+    long long N = 0;              // nodes of the store
+    int slab = 0;                 // 1: z slab with ghost planes 0 and nz - 1 of the store
+    long long NL = 0;             // nodes of the caller's grid
     double nu = 0, omega = 0, rho0 = 1;
     int walls_y = 0;
     int storage = LBM_FP32;
@@ -120,6 +122,8 @@ KParams make_params(const lbm_ctx* c) {
     p.psi = c->psi;
     p.links = c->links;
     p.flag = c->flag_dev;
+    p.z0 = c->slab;
+    p.local_off = (long long)c->slab * c->nx * c->ny;
     return p;
 }
 
@@ -189,7 +193,7 @@ lbm_status sync_and_check(lbm_ctx* c) {
 }
 
 lbm_status ensure_macro(lbm_ctx* c) {
-    if (!c->macro) CK(c, cudaMalloc(&c->macro, sizeof(float) * 4 * c->N), "cudaMalloc(macroscopic)");
+    if (!c->macro) CK(c, cudaMalloc(&c->macro, sizeof(float) * 4 * c->NL), "cudaMalloc(macroscopic)");
     return LBM_OK;
 }
 
@@ -207,7 +211,8 @@ lbm_status run_macro(lbm_ctx* c) {
     st = refresh_psi(c, p);
     if (st) return st;
     float* m = c->macro;
-    CK(c, DISPATCH(c, launch_macroscopic, p, c->f, c->parity, kernel_force_kind(c), m, m + c->N, m + 2 * c->N, m + 3 * c->N,
+    const long long NL = c->NL;
+    CK(c, DISPATCH(c, launch_macroscopic, p, c->f, c->parity, kernel_force_kind(c), m, m + NL, m + 2 * NL, m + 3 * NL,
                    c->stream),
        "macroscopic kernel");
     return LBM_OK;
@@ -269,7 +274,8 @@ extern "C" {
 
 size_t lbm_store_bytes(const lbm_desc* d) {
     if (!valid_dims(d) || d->storage < LBM_FP32 || d->storage > LBM_BF16_DEV) return 0;
-    return (size_t)27 * (size_t)d->nx * (size_t)d->ny * (size_t)d->nz * elem_size(d->storage);
+    const size_t planes = (size_t)d->nz + (d->slab_z ? 2 : 0);
+    return (size_t)27 * (size_t)d->nx * (size_t)d->ny * planes * elem_size(d->storage);
 }
 
 lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
@@ -281,13 +287,16 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
     if (d->storage < LBM_FP32 || d->storage > LBM_BF16_DEV) return fail(nullptr, LBM_ERR_ARG, "unknown storage");
     if (d->store && (reinterpret_cast<uintptr_t>(d->store) % 256) != 0)
         return fail(nullptr, LBM_ERR_ARG, "store must be 256-byte aligned");
+    if (d->slab_z && d->mask) return fail(nullptr, LBM_ERR_UNSUPPORTED, "z slabs do not take solid masks");
 
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    c->slab = d->slab_z ? 1 : 0;
     c->nx = d->nx;
     c->ny = d->ny;
-    c->nz = d->nz;
-    c->N = (long long)d->nx * d->ny * d->nz;
+    c->nz = d->nz + 2 * c->slab;
+    c->N = (long long)d->nx * d->ny * c->nz;
+    c->NL = (long long)d->nx * d->ny * d->nz;
     c->nu = d->nu;
     c->omega = 1.0 / (3.0 * d->nu + 0.5);  // omega = (nu / c_s^2 + 1/2)^-1, Sec. II
     c->rho0 = d->rho0;
@@ -365,6 +374,7 @@ lbm_status lbm_set_force(lbm_ctx* c, int kind, const double* params, const float
     }
     case LBM_FORCE_FIELD: {
         if (!fx || !fy || !fz) return fail(c, LBM_ERR_ARG, "FIELD needs fx, fy, fz");
+        if (c->slab) return fail(c, LBM_ERR_UNSUPPORTED, "z slabs take uniform or Kolmogorov forces");
         if (!c->field) CK(c, cudaMalloc(&c->field, sizeof(float) * 3 * c->N), "cudaMalloc(force field)");
         const size_t b = sizeof(float) * c->N;
         CK(c, copy_in(c->field, fx, b, c->stream), "force copy");
@@ -375,7 +385,8 @@ lbm_status lbm_set_force(lbm_ctx* c, int kind, const double* params, const float
     }
     case LBM_FORCE_SHAN_CHEN:
         if (!params) return fail(c, LBM_ERR_ARG, "SHAN_CHEN needs params[0] = G");
-        if (c->walls_y || c->links) return fail(c, LBM_ERR_UNSUPPORTED, "Shan-Chen force needs a fully periodic domain");
+        if (c->walls_y || c->links || c->slab)
+            return fail(c, LBM_ERR_UNSUPPORTED, "Shan-Chen force needs a fully periodic single domain");
         c->G = (float)params[0];
         if (!c->psi) CK(c, cudaMalloc(&c->psi, sizeof(float) * c->N), "cudaMalloc(psi)");
         break;
@@ -391,14 +402,15 @@ lbm_status lbm_set_state(lbm_ctx* c, const float* rho, const float* ux, const fl
     if (!rho || !ux || !uy || !uz) return fail(c, LBM_ERR_ARG, "rho, ux, uy, uz are required");
     lbm_status st = ensure_macro(c);
     if (st) return st;
-    const size_t b = sizeof(float) * c->N;
+    const long long NL = c->NL;
+    const size_t b = sizeof(float) * NL;
     float* m = c->macro;
     CK(c, copy_in(m, rho, b, c->stream), "state copy");
-    CK(c, copy_in(m + c->N, ux, b, c->stream), "state copy");
-    CK(c, copy_in(m + 2 * c->N, uy, b, c->stream), "state copy");
-    CK(c, copy_in(m + 3 * c->N, uz, b, c->stream), "state copy");
+    CK(c, copy_in(m + NL, ux, b, c->stream), "state copy");
+    CK(c, copy_in(m + 2 * NL, uy, b, c->stream), "state copy");
+    CK(c, copy_in(m + 3 * NL, uz, b, c->stream), "state copy");
     KParams p = make_params(c);
-    CK(c, DISPATCH(c, launch_init_equilibrium, p, c->f, m, m + c->N, m + 2 * c->N, m + 3 * c->N, c->stream), "init kernel");
+    CK(c, DISPATCH(c, launch_init_equilibrium, p, c->f, m, m + NL, m + 2 * NL, m + 3 * NL, c->stream), "init kernel");
     CK(c, cudaStreamSynchronize(c->stream), "init sync");
     c->parity = 0;
     c->t = 0;
@@ -412,8 +424,8 @@ lbm_status lbm_set_populations(lbm_ctx* c, const float* g) {
     const float* src = g;
     float* tmp = nullptr;
     if (!is_device_ptr(g)) {
-        CK(c, cudaMalloc(&tmp, sizeof(float) * 27 * c->N), "cudaMalloc(staging)");
-        cudaError_t e = cudaMemcpyAsync(tmp, g, sizeof(float) * 27 * c->N, cudaMemcpyHostToDevice, c->stream);
+        CK(c, cudaMalloc(&tmp, sizeof(float) * 27 * c->NL), "cudaMalloc(staging)");
+        cudaError_t e = cudaMemcpyAsync(tmp, g, sizeof(float) * 27 * c->NL, cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) {
             cudaFree(tmp);
             return cuda_fail(c, e, "population copy");
@@ -439,12 +451,12 @@ lbm_status lbm_get_populations(lbm_ctx* c, float* g) {
     float* tmp = nullptr;
     const bool dev = is_device_ptr(g);
     if (!dev) {
-        CK(c, cudaMalloc(&tmp, sizeof(float) * 27 * c->N), "cudaMalloc(staging)");
+        CK(c, cudaMalloc(&tmp, sizeof(float) * 27 * c->NL), "cudaMalloc(staging)");
         dst = tmp;
     }
     KParams p = make_params(c);
     cudaError_t e = DISPATCH(c, launch_get_populations, p, c->f, c->parity, dst, c->stream);
-    if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(g, tmp, sizeof(float) * 27 * c->N, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(g, tmp, sizeof(float) * 27 * c->NL, cudaMemcpyDeviceToHost, c->stream);
     cudaError_t e2 = cudaStreamSynchronize(c->stream);
     cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(c, e, "get populations");
@@ -472,7 +484,7 @@ lbm_status lbm_macroscopic(lbm_ctx* c, float* rho, float* ux, float* uy, float* 
     if (st) return st;
     float* outs[4] = {rho, ux, uy, uz};
     for (int k = 0; k < 4; ++k)
-        if (outs[k]) CK(c, copy_out(outs[k], c->macro + k * c->N, sizeof(float) * c->N, c->stream), "macroscopic copy");
+        if (outs[k]) CK(c, copy_out(outs[k], c->macro + k * c->NL, sizeof(float) * c->NL, c->stream), "macroscopic copy");
     return sync_and_check(c);
 }
 
@@ -481,9 +493,9 @@ lbm_status lbm_stats(lbm_ctx* c, double* out) {
     if (!out) return fail(c, LBM_ERR_ARG, "out is NULL");
     lbm_status st = run_macro(c);
     if (st) return st;
-    if (!c->uprev) CK(c, cudaMalloc(&c->uprev, sizeof(float) * 3 * c->N), "cudaMalloc(u_prev)");
+    if (!c->uprev) CK(c, cudaMalloc(&c->uprev, sizeof(float) * 3 * c->NL), "cudaMalloc(u_prev)");
     if (!c->partials) {
-        c->nblocks = reduce_blocks(c->N);
+        c->nblocks = reduce_blocks(c->NL);
         CK(c, cudaMalloc(&c->partials, sizeof(double) * REDUCE_FIELDS * c->nblocks), "cudaMalloc(partials)");
         CK(c, cudaMalloc(&c->stats_dev, sizeof(double) * REDUCE_FIELDS), "cudaMalloc(stats)");
         CK(c, cudaMallocHost(&c->stats_host, sizeof(double) * REDUCE_FIELDS), "cudaMallocHost(stats)");
@@ -491,18 +503,18 @@ lbm_status lbm_stats(lbm_ctx* c, double* out) {
     ReduceArgs a;
     a.nx = c->nx;
     a.ny = c->ny;
-    a.nz = c->nz;
+    a.nz = c->nz - 2 * c->slab;
     a.walls_y = c->walls_y;
-    a.links = c->links;
+    a.links = c->links ? c->links + (long long)c->slab * c->nx * c->ny : nullptr;
     a.rho = c->macro;
-    a.ux = c->macro + c->N;
-    a.uy = c->macro + 2 * c->N;
-    a.uz = c->macro + 3 * c->N;
+    a.ux = c->macro + c->NL;
+    a.uy = c->macro + 2 * c->NL;
+    a.uz = c->macro + 3 * c->NL;
     a.uprev = c->have_uprev ? c->uprev : nullptr;
     CK(c, launch_reduce(a, c->partials, c->nblocks, c->stats_dev, c->stream), "reduce kernels");
     CK(c, cudaMemcpyAsync(c->stats_host, c->stats_dev, sizeof(double) * REDUCE_FIELDS, cudaMemcpyDeviceToHost, c->stream),
        "stats copy");
-    CK(c, cudaMemcpyAsync(c->uprev, c->macro + c->N, sizeof(float) * 3 * c->N, cudaMemcpyDeviceToDevice, c->stream),
+    CK(c, cudaMemcpyAsync(c->uprev, c->macro + c->NL, sizeof(float) * 3 * c->NL, cudaMemcpyDeviceToDevice, c->stream),
        "u_prev copy");
     st = sync_and_check(c);
     c->have_uprev = true;
@@ -525,6 +537,43 @@ lbm_status lbm_synchronize(lbm_ctx* c) {
     if (!c) return LBM_ERR_ARG;
     return sync_and_check(c);
 }
+
+size_t lbm_halo_bytes(const lbm_ctx* c) {
+    if (!c || !c->slab) return 0;
+    return (size_t)9 * (size_t)c->nx * (size_t)c->ny * elem_size(c->storage);
+}
+
+// (store plane, c_z sign) of the 9 slot planes a face exchanges at a stage of an odd step
+static void halo_plane(const lbm_ctx* c, int face, int stage, int pack, int* zs, int* sz) {
+    const int top = c->nz - 1;  // store planes: 0 ghost, 1 .. nz-2 active, nz-1 ghost
+    if (pack) {
+        if (stage == 0) { *zs = face == 0 ? 1 : top - 1; *sz = face == 0 ? +1 : -1; }
+        else { *zs = face == 0 ? 0 : top; *sz = face == 0 ? -1 : +1; }
+    } else {
+        if (stage == 0) { *zs = face == 0 ? 0 : top; *sz = face == 0 ? -1 : +1; }
+        else { *zs = face == 0 ? 1 : top - 1; *sz = face == 0 ? +1 : -1; }
+    }
+}
+
+static lbm_status halo_copy(lbm_ctx* c, int face, int stage, void* buf, int pack) {
+    if (!c) return LBM_ERR_ARG;
+    if (!c->slab) return fail(c, LBM_ERR_STATE, "not a z slab");
+    if ((face != 0 && face != 1) || (stage != 0 && stage != 1) || !buf) return fail(c, LBM_ERR_ARG, "face, stage in {0, 1}");
+    if (!is_device_ptr(buf)) return fail(c, LBM_ERR_ARG, "halo buffers are device memory");
+    int zs, sz;
+    halo_plane(c, face, stage, pack, &zs, &sz);
+    KParams p = make_params(c);
+    const int skip_blocked = (!pack && stage == 1) ? 1 : 0;
+    CK(c, DISPATCH(c, launch_halo_copy, p, c->f, buf, zs, sz, pack, skip_blocked, c->stream), "halo copy");
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_pack(lbm_ctx* c, int face, int stage, void* buf) { return halo_copy(c, face, stage, buf, 1); }
+lbm_status lbm_halo_unpack(lbm_ctx* c, int face, int stage, const void* buf) {
+    return halo_copy(c, face, stage, const_cast<void*>(buf), 0);
+}
+
+int lbm_parity(const lbm_ctx* c) { return c ? c->parity : -1; }
 
 lbm_status lbm_profile(lbm_ctx* c, int every) {
     if (!c) return LBM_ERR_ARG;

@@ -77,6 +77,8 @@ struct KParams {
     const float* psi;      // FK_SHAN_CHEN: psi = 1 - exp(-rho) of every node
     const uint32_t* links; // bit i: the source x - c_i of direction i is blocked; SOLID_BIT: solid node
     unsigned int* flag;    // set to 1 when a node has rho <= 0, |u| >= 1 or a NaN
+    int z0;                // first active plane of the store (1 for a z slab with ghost planes, else 0)
+    long long local_off;   // z0 * nx * ny: store node index minus caller (local) node index
 };
 
 // Node coordinates and the offsets of its 26 neighbours with periodic wrap in x, y, z.

@@ -26,7 +26,7 @@ __device__ __forceinline__ void check_node(const KParams& p, const Macro& m) {
 template <typename S, bool ODD, bool LINKS, int FK, bool TRACE>
 __global__ void __launch_bounds__(BLOCK_X) k_stream_collide(KParams p, S* __restrict__ f) {
     const int x = blockIdx.x * BLOCK_X + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y, z = blockIdx.z + p.z0;
     if (x >= p.nx) return;
     const Nbr nb(x, y, z, p);
     uint32_t link = 0;
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(BLOCK_X) k_stream_collide(KParams p, S* __rest
 template <typename S, bool ODD, bool LINKS>
 __global__ void __launch_bounds__(BLOCK_X) k_psi(KParams p, const S* __restrict__ f, float* __restrict__ psi) {
     const int x = blockIdx.x * BLOCK_X + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y, z = blockIdx.z + p.z0;
     if (x >= p.nx) return;
     const Nbr nb(x, y, z, p);
     uint32_t link = 0;
@@ -68,16 +68,17 @@ __global__ void __launch_bounds__(BLOCK_X) k_macroscopic(KParams p, const S* __r
                                                          float* __restrict__ ux, float* __restrict__ uy,
                                                          float* __restrict__ uz) {
     const int x = blockIdx.x * BLOCK_X + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y, z = blockIdx.z + p.z0;
     if (x >= p.nx) return;
     const Nbr nb(x, y, z, p);
     const uint32_t n = nb.self();
+    const long long o = (long long)n - p.local_off;  // caller's node index
     uint32_t link = 0;
     if (LINKS) {
         link = p.links[n];
         if (link & SOLID_BIT) {
-            rho[n] = p.rho0;
-            ux[n] = uy[n] = uz[n] = 0.0f;
+            rho[o] = p.rho0;
+            ux[o] = uy[o] = uz[o] = 0.0f;
             return;
         }
     }
@@ -88,17 +89,17 @@ __global__ void __launch_bounds__(BLOCK_X) k_macroscopic(KParams p, const S* __r
     const RawMoments m = raw_moments(g);
     const float r = p.rho0 + m.m000;
     const float inv = 1.0f / r;
-    rho[n] = r;
-    ux[n] = (m.m100 + 0.5f * Fx) * inv;
-    uy[n] = (m.m010 + 0.5f * Fy) * inv;
-    uz[n] = (m.m001 + 0.5f * Fz) * inv;
+    rho[o] = r;
+    ux[o] = (m.m100 + 0.5f * Fx) * inv;
+    uy[o] = (m.m010 + 0.5f * Fy) * inv;
+    uz[o] = (m.m001 + 0.5f * Fz) * inv;
 }
 
 // Populations at the current time in natural order, as FP32 deviations out[i*N + n].
 template <typename S, bool ODD, bool LINKS>
 __global__ void __launch_bounds__(BLOCK_X) k_get_populations(KParams p, const S* __restrict__ f, float* __restrict__ out) {
     const int x = blockIdx.x * BLOCK_X + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y, z = blockIdx.z + p.z0;
     if (x >= p.nx) return;
     const Nbr nb(x, y, z, p);
     const uint32_t n = nb.self();
@@ -109,16 +110,21 @@ __global__ void __launch_bounds__(BLOCK_X) k_get_populations(KParams p, const S*
         aa_gather<S, false, false>(f, p.N, nb, 0u, g);
     else
         aa_gather<S, ODD, LINKS>(f, p.N, nb, link, g);
+    const long long nl = p.N - 2 * p.local_off;  // nodes of the caller's grid
 #pragma unroll
-    for (int i = 0; i < 27; ++i) out[(long long)i * p.N + n] = g[i];
+    for (int i = 0; i < 27; ++i) out[(long long)i * nl + ((long long)n - p.local_off)] = g[i];
 }
 
 // Natural-order store of FP32 deviations (leaves the store in even parity).
 template <typename S>
 __global__ void __launch_bounds__(BLOCK_X) k_set_populations(KParams p, S* __restrict__ f, const float* __restrict__ in) {
-    const long long i0 = (long long)blockIdx.x * BLOCK_X + threadIdx.x;
-    const long long total = 27LL * p.N;
-    for (long long k = i0; k < total; k += (long long)gridDim.x * BLOCK_X) Codec<S>::st(f + k, in[k]);
+    const int x = blockIdx.x * BLOCK_X + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z + p.z0;
+    if (x >= p.nx) return;
+    const long long n = (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
+    const long long nl = p.N - 2 * p.local_off;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) Codec<S>::st(f + (long long)i * p.N + n, in[(long long)i * nl + (n - p.local_off)]);
 }
 
 // K5: f = f^eq(rho, u) (complete equilibrium, product form) on fluid nodes, rest state on solids.
@@ -127,19 +133,23 @@ __global__ void __launch_bounds__(BLOCK_X) k_init_equilibrium(KParams p, S* __re
                                                               const float* __restrict__ ux, const float* __restrict__ uy,
                                                               const float* __restrict__ uz) {
     const int x = blockIdx.x * BLOCK_X + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y, z = blockIdx.z + p.z0;
     if (x >= p.nx) return;
     const uint32_t n = (uint32_t)x + (uint32_t)p.nx * ((uint32_t)y + (uint32_t)p.ny * (uint32_t)z);
+    const long long o = (long long)n - p.local_off;
     float g[27];
     if (p.links && (p.links[n] & SOLID_BIT))
         equilibrium_dev(p.rho0, 0.0f, 0.0f, 0.0f, p.rho0, g);
     else
-        equilibrium_dev(rho[n], ux[n], uy[n], uz[n], p.rho0, g);
+        equilibrium_dev(rho[o], ux[o], uy[o], uz[o], p.rho0, g);
 #pragma unroll
     for (int i = 0; i < 27; ++i) Codec<S>::st(f + (long long)i * p.N + n, g[i]);
 }
 
-static inline dim3 node_grid(const KParams& p) { return dim3((p.nx + BLOCK_X - 1) / BLOCK_X, p.ny, p.nz); }
+// one block row per active (y, z) line: the ghost planes of a z slab get no threads
+static inline dim3 node_grid(const KParams& p) {
+    return dim3((p.nx + BLOCK_X - 1) / BLOCK_X, p.ny, p.nz - 2 * p.z0);
+}
 
 // ----------------------------------------------------------------------------- launchers
 template <typename S, bool ODD, bool LINKS>
@@ -227,10 +237,38 @@ cudaError_t launch_get_populations(const KParams& p, const void* f, int odd, flo
 
 template <typename S>
 cudaError_t launch_set_populations(const KParams& p, void* f, const float* in, cudaStream_t st) {
-    const long long total = 27LL * p.N;
-    long long blocks = (total + BLOCK_X - 1) / BLOCK_X;
-    if (blocks > 152LL * 64) blocks = 152LL * 64;
-    k_set_populations<S><<<(unsigned)blocks, BLOCK_X, 0, st>>>(p, static_cast<S*>(f), in);
+    k_set_populations<S><<<node_grid(p), BLOCK_X, 0, st>>>(p, static_cast<S*>(f), in);
+    return cudaGetLastError();
+}
+
+// z-slab halo: copies the 9 slot planes of direction sign sz (c_z = sz) of store plane zs to or
+// from a contiguous buffer of 9 * nx * ny elements (raw storage values).  skip_blocked (the
+// unpack after an odd step) leaves alone every slot whose direction's source is blocked (link
+// bit set): such a slot has no pusher across the face -- it holds this node's own bounce-back.
+template <typename S>
+__global__ void k_halo_copy(KParams p, S* __restrict__ f, S* __restrict__ buf, int zs, int sz, int to_buf,
+                            int skip_blocked) {
+    const long long plane = (long long)p.nx * p.ny;
+    const long long total = 9 * plane;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(k / plane);
+        const long long node = (long long)zs * plane + (k % plane);
+        int slot = 0, seen = 0;
+        for (int i = 0; i < 27; ++i)
+            if (dir_z(i) == sz) {
+                if (seen == j) slot = i;
+                ++seen;
+            }
+        S* a = f + (long long)slot * p.N + node;
+        if (to_buf) buf[k] = *a;
+        else if (!(skip_blocked && p.links && ((p.links[node] >> slot) & 1u))) *a = buf[k];
+    }
+}
+
+template <typename S>
+cudaError_t launch_halo_copy(const KParams& p, void* f, void* buf, int zs, int sz, int to_buf, int skip_blocked,
+                             cudaStream_t st) {
+    k_halo_copy<S><<<152 * 4, 256, 0, st>>>(p, static_cast<S*>(f), static_cast<S*>(buf), zs, sz, to_buf, skip_blocked);
     return cudaGetLastError();
 }
 
@@ -257,4 +295,5 @@ cudaError_t launch_init_equilibrium(const KParams& p, void* f, const float* rho,
     template cudaError_t launch_set_populations<S>(const KParams&, void*, const float*, cudaStream_t);           \
     template cudaError_t launch_init_equilibrium<S>(const KParams&, void*, const float*, const float*,           \
                                                     const float*, const float*, cudaStream_t);                   \
+    template cudaError_t launch_halo_copy<S>(const KParams&, void*, void*, int, int, int, int, cudaStream_t);      \
     }

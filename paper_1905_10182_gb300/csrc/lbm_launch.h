@@ -27,6 +27,10 @@ template <typename S>
 cudaError_t launch_init_equilibrium(const KParams& p, void* f, const float* rho, const float* ux, const float* uy,
                                     const float* uz, cudaStream_t st);
 
+template <typename S>
+cudaError_t launch_halo_copy(const KParams& p, void* f, void* buf, int zs, int sz, int to_buf, int skip_blocked,
+                             cudaStream_t st);
+
 // lbm_reduce.cu: FP64 diagnostics over the macroscopic fields
 struct ReduceArgs {
     int nx, ny, nz;

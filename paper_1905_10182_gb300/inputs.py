@@ -136,3 +136,13 @@ def porous_channel(seed, size_lo=(32, 32, 32), size_hi=(96, 48, 96)):
     fx = rng.uniform(1e-6, 1e-5)
     mask, phi = sphere_pack(nx, ny, nz, seed)
     return dict(nx=nx, ny=ny, nz=nz, nu=nu, fx=fx, mask=mask, phi_target=phi, seed=seed)
+
+
+def porous_cube(seed, n=64):
+    """A forced porous channel on an n^3 grid for the learned warm start: walls in y, sphere-pack
+    obstacles (solid fraction target U[0, 0.2]), nu ~ U[0.01, 0.1], F_x ~ U[1e-6, 1e-5]."""
+    rng = SplitMix(2_000_003 + seed)
+    nu = rng.uniform(0.01, 0.1)
+    fx = rng.uniform(1e-6, 1e-5)
+    mask, phi = sphere_pack(n, n, n, 7_000_001 + seed)
+    return dict(nx=n, ny=n, nz=n, nu=nu, fx=fx, mask=mask, phi_target=phi, seed=seed)

@@ -30,7 +30,7 @@ class Solver:
     """One D3Q27 central-moment LBM domain on the current CUDA device."""
 
     def __init__(self, nx, ny, nz, nu, rho0=1.0, walls_y=False, mask=None, storage="fp32", stream=None,
-                 torch_store=True):
+                 torch_store=True, slab_z=False):
         self._lib = nat.lib()
         self.shape = (int(nz), int(ny), int(nx))
         self.N = int(nx) * int(ny) * int(nz)
@@ -47,6 +47,7 @@ class Solver:
                 self._mask = np.ascontiguousarray(mask, dtype=np.uint8)
             d.mask = nat.ptr(self._mask)
         d.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        d.slab_z = int(bool(slab_z))
         self.storage = storage
         self._store = None
         if stream is None or torch_store:
@@ -130,6 +131,21 @@ class Solver:
         keys = ("mass", "mom_x", "mom_y", "mom_z", "residual", "kinetic_energy", "enstrophy", "umax",
                 "fluid_nodes", "step")
         return dict(zip(keys, list(out)))
+
+    # -- z slabs (see paper_1905_10182_gb300.slabs)
+    @property
+    def halo_bytes(self):
+        return self._lib.lbm_halo_bytes(self._h)
+
+    @property
+    def parity(self):
+        return self._lib.lbm_parity(self._h)
+
+    def halo_pack(self, face, stage, buf):
+        self._check(self._lib.lbm_halo_pack(self._h, int(face), int(stage), nat.ptr(buf)))
+
+    def halo_unpack(self, face, stage, buf):
+        self._check(self._lib.lbm_halo_unpack(self._h, int(face), int(stage), nat.ptr(buf)))
 
     def profile(self, every=1):
         """Record kernel times of every every-th step (0: off)."""

@@ -1,0 +1,109 @@
+"""Physics of the benchmark configurations on the GPU path (through the C ABI).
+
+* Four-rolls mill (Sec. III A, run in 2D with nz = 1): second-order convergence to the closed form;
+  the paper reports a rate of 1.998 (tests/golden/four_rolls_mill.txt).
+* Static droplet with the Shan-Chen force (Sec. III, static droplet): Laplace's law dp = 2 sigma / R
+  at 128^3 for R = 16, 24, 32, and the same surface tension from the FP64 oracle at 32^3.
+* Decaying Taylor-Green vortex: the kinetic-energy decay rate equals -2 nu x enstrophy (energy
+  equation of periodic incompressible flow), both taken from the FP64 diagnostics of lbm_stats.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from golden_util import load_table  # noqa: E402
+from paper_1905_10182_gb300 import Solver, inputs  # noqa: E402
+
+
+def _four_rolls_error(N, u0=1e-3, Re=100.0):
+    nu = u0 * N / Re
+    psi = 2 * math.pi / N
+    x = np.arange(N)
+    X, Y = np.meshgrid(x, x, indexing="xy")  # [y][x]
+    Fx = 2 * nu * u0 * psi ** 2 * np.sin(psi * X) * np.sin(psi * Y)
+    Fy = 2 * nu * u0 * psi ** 2 * np.cos(psi * X) * np.cos(psi * Y)
+    ux_an = u0 * np.sin(psi * X) * np.sin(psi * Y)
+    uy_an = u0 * np.cos(psi * X) * np.cos(psi * Y)
+    s = Solver(N, N, 1, nu=nu)
+    z = np.zeros((1, N, N), np.float32)
+    s.set_force("field", None, Fx[None].astype(np.float32), Fy[None].astype(np.float32), z)
+    s.set_state(np.ones((1, N, N), np.float32), ux_an[None].astype(np.float32), uy_an[None].astype(np.float32), z)
+    lam = 2 * nu * psi ** 2  # decay rate of the slowest transient
+    s.step(int(12.0 / lam))
+    _, ux, uy, _ = s.macroscopic()
+    num = np.concatenate([ux[0].ravel(), uy[0].ravel()]).astype(np.float64)
+    an = np.concatenate([ux_an.ravel(), uy_an.ravel()])
+    return np.linalg.norm(num - an) / np.linalg.norm(an)
+
+
+def test_four_rolls_mill_second_order():
+    paper_rate = float(load_table("four_rolls_mill.txt")["rate"])
+    errs = [_four_rolls_error(N) for N in (16, 32, 64)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    print(f"four-rolls mill errors {errs}, rates {rates} (paper: {paper_rate})")
+    assert all(abs(r - paper_rate) < 0.1 for r in rates), (errs, rates)
+
+
+def _laplace(rho, G, n):
+    """dp between centre and far corner (p = rho/3 + G psi^2/6) and the volume-equivalent radius."""
+    psi = 1.0 - np.exp(-rho.astype(np.float64))
+    p = rho / 3.0 + G * psi ** 2 / 6.0
+    c = n // 2
+    rl, rg = float(rho[c, c, c]), float(rho[0, 0, 0])
+    dp = float(p[c, c, c] - p[0, 0, 0])
+    V = (rho.astype(np.float64).sum() - rg * n ** 3) / (rl - rg)
+    return dp, (3 * V / (4 * math.pi)) ** (1.0 / 3.0)
+
+
+def test_droplet_laplace_law_and_oracle_surface_tension(orc):
+    G, n = -5.5, 128
+    sig = []
+    for R in (16, 24, 32):
+        s = Solver(n, n, n, nu=1 / 6)
+        s.set_force("shan_chen", (G,))
+        z = np.zeros((n, n, n), np.float32)
+        s.set_state(inputs.droplet_density(n, R), z, z, z)
+        s.step(20000)
+        rho, *_ = s.macroscopic()
+        dp, Reff = _laplace(rho, G, n)
+        sig.append(dp * Reff / 2.0)
+    sig = np.array(sig)
+    print(f"GPU 128^3 surface tension per radius: {sig}")
+    assert sig.std() / sig.mean() < 0.05  # dp R constant: Laplace's law
+    # the FP64 oracle at 32^3 (R = 6, 8, 10)
+    m = 32
+    so = []
+    for R in (6, 8, 10):
+        g = orc.Grid(m, m, m, nu=1 / 6, force_kind=orc.FORCE_SHAN_CHEN, G=G, collision=orc.COLL_PAPER)
+        f = g.init_equilibrium(inputs.droplet_density(m, R).astype(np.float64), np.zeros((3, m, m, m)))
+        rho, _ = g.macroscopic(g.step(f, 4000))
+        dp, Reff = _laplace(rho, G, m)
+        so.append(dp * Reff / 2.0)
+    so = np.array(so)
+    print(f"oracle 32^3 surface tension per radius: {so}")
+    assert abs(sig.mean() - so.mean()) / so.mean() < 0.15
+
+
+def test_taylor_green_energy_decay_rate():
+    n, u0, nu = 64, 0.05, 0.005
+    rho, ux, uy, uz = inputs.taylor_green(n, u0)
+    s = Solver(n, n, n, nu=nu)
+    s.set_state(rho, ux, uy, uz)
+    s.step(200)
+    d = 20
+    e0 = s.stats()["kinetic_energy"]
+    s.step(d)
+    st = s.stats()
+    s.step(d)
+    e2 = s.stats()["kinetic_energy"]
+    rate = (e2 - e0) / (2 * d)
+    expect = -2.0 * nu * st["enstrophy"]
+    print(f"TGV dE/dt = {rate:.6e}, -2 nu Omega = {expect:.6e}")
+    assert rate == pytest.approx(expect, rel=0.03)
