@@ -53,7 +53,10 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="droplet128")
     ap.add_argument("--storage", choices=["fp32", "fp16", "bf16"], default="fp32")
     ap.add_argument("--n", type=int, default=None, help="override the cube edge (profiling of smaller cases)")
+    ap.add_argument("--count", type=int, default=None, help="override the number of batched domains")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--budget-s", type=float, default=60.0,
+                    help="reference arm: wall-time budget of warm-up plus timed oracle steps")
     return ap.parse_args()
 
 
@@ -189,7 +192,7 @@ def run_reference(args, wl):
     m = 16
     probe = oracle_mlups(dict(wl, n=min(wl["n"], 32)), target_s=1.0, threads=threads)
     per_node = 1.0 / (probe["value"] * 1e6)
-    budget = 60.0 / max(1, args.steps + args.warmup)
+    budget = args.budget_s / max(1, args.steps + args.warmup)
     m = int(max(8, min(wl["n"], (budget / per_node) ** (1.0 / 3.0))))
     sub = dict(wl, n=m)
     if wl["kind"] == "droplet":
@@ -462,6 +465,9 @@ def run_ours(args, wl):
 def main():
     args = parse()
     wl = dict(WORKLOADS[args.workload])
+    if args.count and wl["kind"] == "porous":
+        wl["count"] = args.count
+        wl["text"] = wl["text"].replace("512 forced", f"{args.count} forced")
     if args.n:
         if wl["kind"] == "droplet":
             wl["radius"] = wl["radius"] * args.n / wl["n"]

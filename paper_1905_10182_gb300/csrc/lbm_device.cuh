@@ -401,6 +401,53 @@ __device__ __forceinline__ Macro collide_cm(float (&g)[27], float Fx, float Fy, 
     return m;
 }
 
+// Direct form of the same collision, f* = (T^T)^-1 k* (Eq. system) with k* of
+// Eq. post_collision_central_moments_forcing, used with 16-bit storage: it needs only the ten raw
+// moments of order <= 2 and one inverse transform, and its FP32 rounding (a few ulp of |g| per
+// step) stays far below the 2^-11 / 2^-8 rounding of FP16 / BF16 storage.
+__device__ __forceinline__ Macro collide_cm_direct(float (&g)[27], float Fx, float Fy, float Fz, float omega,
+                                                   float rho0) {
+    const RawMoments m = raw_moments(g);
+    const float dr = m.m000;
+    const float rho = rho0 + dr;
+    const float inv = 1.0f / rho;
+    const float ux = (m.m100 + 0.5f * Fx) * inv;
+    const float uy = (m.m010 + 0.5f * Fy) * inv;
+    const float uz = (m.m001 + 0.5f * Fz) * inv;
+    const float k4 = m.m110 - rho * ux * uy + 0.5f * (ux * Fy + uy * Fx);
+    const float k5 = m.m101 - rho * ux * uz + 0.5f * (ux * Fz + uz * Fx);
+    const float k6 = m.m011 - rho * uy * uz + 0.5f * (uy * Fz + uz * Fy);
+    const float uFx = ux * Fx, uFy = uy * Fy, uFz = uz * Fz;
+    const float k7 = (m.m200 - m.m020) - rho * (ux * ux - uy * uy) + uFx - uFy;
+    const float k8 = (m.m200 - m.m002) - rho * (ux * ux - uz * uz) + uFx - uFz;
+    const float om1 = 1.0f - omega;
+    const float k7s = om1 * k7, k8s = om1 * k8;
+    const float third = 1.0f / 3.0f;
+    float kd[3][3][3];  // post-collision central moments minus the rest-state moments
+    kd[0][0][0] = dr;
+    kd[1][0][0] = 0.5f * Fx;
+    kd[0][1][0] = 0.5f * Fy;
+    kd[0][0][1] = 0.5f * Fz;
+    kd[1][1][0] = om1 * k4;
+    kd[1][0][1] = om1 * k5;
+    kd[0][1][1] = om1 * k6;
+    kd[2][0][0] = (k7s + k8s + dr) * third;
+    kd[0][2][0] = (dr - 2.0f * k7s + k8s) * third;
+    kd[0][0][2] = (dr + k7s - 2.0f * k8s) * third;
+    kd[1][2][0] = kd[1][0][2] = Fx * (1.0f / 6.0f);
+    kd[2][1][0] = kd[0][1][2] = Fy * (1.0f / 6.0f);
+    kd[2][0][1] = kd[0][2][1] = Fz * (1.0f / 6.0f);
+    kd[1][1][1] = 0.0f;
+    kd[2][2][0] = kd[2][0][2] = kd[0][2][2] = dr * (1.0f / 9.0f);
+    kd[2][1][1] = kd[1][2][1] = kd[1][1][2] = 0.0f;
+    kd[1][2][2] = Fx * (1.0f / 18.0f);
+    kd[2][1][2] = Fy * (1.0f / 18.0f);
+    kd[2][2][1] = Fz * (1.0f / 18.0f);
+    kd[2][2][2] = dr * (1.0f / 27.0f);
+    inverse_fast_dev(kd, ux, uy, uz, rho0, g);
+    return Macro{rho, ux, uy, uz};
+}
+
 // Equilibrium deviations g_i = f_i^eq(rho, u) - w_i rho0: the equilibrium CMs of
 // Eq. equil_central_moments6 are rho * s_a s_b s_c, so the inverse runs on (rho - rho0) s_a s_b s_c.
 __device__ __forceinline__ void equilibrium_dev(float rho, float ux, float uy, float uz, float rho0, float (&g)[27]) {

@@ -23,10 +23,44 @@ __device__ __forceinline__ void check_node(const KParams& p, const Macro& m) {
 
 // K1: one fused AA stream-collide step.  TRACE replaces the collision by the identity, which
 // turns the step into pure streaming with bounce-back (used to check indices bit-exactly).
+// Shan-Chen stencil from a shared-memory tile: the block's row segment of psi with one node of
+// x halo, for the 3 x 3 rows (y - 1 .. y + 1, z - 1 .. z + 1) around it.
+__device__ __forceinline__ void sc_force_tile(const KParams& p, const float (*tile)[BLOCK_X + 2], int t, float& Fx,
+                                              float& Fy, float& Fz) {
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 27; ++i) {
+        const float v = tile[(dir_z(i) + 1) * 3 + dir_y(i) + 1][t + 1 + dir_x(i)];
+        if (dir_x(i)) sx = fmaf(dir_x(i) > 0 ? weight(i) : -weight(i), v, sx);
+        if (dir_y(i)) sy = fmaf(dir_y(i) > 0 ? weight(i) : -weight(i), v, sy);
+        if (dir_z(i)) sz = fmaf(dir_z(i) > 0 ? weight(i) : -weight(i), v, sz);
+    }
+    const float a = -p.G * tile[4][t + 1];
+    Fx = a * sx;
+    Fy = a * sy;
+    Fz = a * sz;
+}
+
 template <typename S, bool ODD, bool LINKS, int FK, bool TRACE>
-__global__ void __launch_bounds__(BLOCK_X) k_stream_collide(KParams p, S* __restrict__ f) {
+__global__ void __launch_bounds__(BLOCK_X, (sizeof(S) == 4 ? 4 : 5)) k_stream_collide(KParams p, S* __restrict__ f) {
     const int x = blockIdx.x * BLOCK_X + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z + p.z0;
+    // Shan-Chen: stage the psi rows of the stencil once per block (before any thread leaves)
+    __shared__ float psi_tile[(FK == FK_SHAN_CHEN && !TRACE) ? 9 : 1][BLOCK_X + 2];
+    if constexpr (FK == FK_SHAN_CHEN && !TRACE) {
+        const int x0 = blockIdx.x * BLOCK_X;
+        const uint32_t nx = p.nx, ny = p.ny, nz = p.nz;
+        for (int k = threadIdx.x; k < 9 * (BLOCK_X + 2); k += BLOCK_X) {
+            const int r = k / (BLOCK_X + 2), c = k % (BLOCK_X + 2);
+            const int xx = x0 + c - 1;
+            if (xx > (int)nx) continue;  // beyond the row end and its halo node
+            const uint32_t xw = xx < 0 ? nx - 1 : (xx >= (int)nx ? 0 : (uint32_t)xx);
+            const int dy = r % 3 - 1, dz = r / 3 - 1;
+            const uint32_t yw = (uint32_t)((y + dy + (int)ny) % (int)ny), zw = (uint32_t)((z + dz + (int)nz) % (int)nz);
+            psi_tile[r][c] = p.psi[xw + nx * (yw + ny * zw)];
+        }
+        __syncthreads();
+    }
     if (x >= p.nx) return;
     const Nbr nb(x, y, z, p);
     uint32_t link = 0;
@@ -38,8 +72,16 @@ __global__ void __launch_bounds__(BLOCK_X) k_stream_collide(KParams p, S* __rest
     aa_gather<S, ODD, LINKS>(f, p.N, nb, link, g);
     if (!TRACE) {
         float Fx, Fy, Fz;
-        node_force<FK>(p, nb, y, Fx, Fy, Fz);
-        const Macro m = collide_cm(g, Fx, Fy, Fz, p.omega, p.rho0);
+        if constexpr (FK == FK_SHAN_CHEN)
+            sc_force_tile(p, psi_tile, threadIdx.x, Fx, Fy, Fz);
+        else
+            node_force<FK>(p, nb, y, Fx, Fy, Fz);
+        // FP32 storage: increment form (rounding scales with the change); 16-bit: direct form
+        Macro m;
+        if constexpr (sizeof(S) == 4)
+            m = collide_cm(g, Fx, Fy, Fz, p.omega, p.rho0);
+        else
+            m = collide_cm_direct(g, Fx, Fy, Fz, p.omega, p.rho0);
         check_node(p, m);
     }
     aa_scatter<S, ODD, LINKS>(f, p.N, nb, link, g);
