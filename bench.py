@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "D3Q27 CM-LBM MLUPS & HBM roofline fraction; time-to-steady warm vs plain"
-PROFILE_EVERY = 8  # kernel times of every 8th step are recorded inside the timed region
+PROFILE_EVERY = 8  # kernel times of the step pairs t = 0, 1 (mod 8) are recorded inside the timed region
 BYTES_PER_NODE = {"fp32": 216, "fp16": 108, "bf16": 108}  # AA in place: 27 reads + 27 writes
 
 WORKLOADS = {
@@ -224,10 +224,13 @@ def run_reference(args, wl):
 
 # --------------------------------------------------------------------------- our arm
 def kernel_source_hash():
+    """Hash of the sources the single-domain stream-collide kernels are built from (device
+    building blocks, kernel templates and their instantiation units)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1905_10182_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name in ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_x2.cuh", "lbm_launch.h") or \
+                (name.startswith("lbm_k_") and name.endswith(".cu")):
             h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -427,7 +430,8 @@ def run_ours(args, wl):
     coll_avg_ms = prof["collide_ms"] / max(1, prof["collide_launches"])
     achieved = bpn * nodes / (coll_avg_ms * 1e-3) / 1e9
     traffic = committed_traffic(args.workload, args.storage)
-    launches = prof["collide_launches"] + prof["psi_launches"]
+    # every kernel launched in the timed region: one stream-collide per step, plus psi (Shan-Chen)
+    launches = args.steps * (2 if prof["psi_launches"] else 1)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:

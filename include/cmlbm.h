@@ -107,6 +107,18 @@ LBM_API lbm_status lbm_create(const lbm_desc* desc, lbm_ctx** out);
 LBM_API lbm_status lbm_set_force(lbm_ctx* ctx, int kind, const double* params, const float* fx, const float* fy,
                          const float* fz);
 
+/* Hermite truncation orders of the equilibrium (Eq. eq:truncation) and of the forcing term
+ * (Eq. generalForcing) used by the collision, among the models compared in Sec. III:
+ *   (6, 6)  complete expansions, the present method M1 (the default);
+ *   (6, 2)  complete equilibrium, second-order (Guo) forcing term: M4;
+ *   (2, 2)  classical second-order equilibrium and forcing term: M5;
+ *   (2, 6)  second-order equilibrium with the complete forcing term.
+ * With either order at 2 the central moments of order >= 3 (relaxed at rate 1) take the
+ * velocity-dependent values of the truncated expansions; k0..k9 are unchanged.  Takes effect at
+ * the next step; lbm_set_state keeps using the complete equilibrium (all truncations agree at
+ * u = 0).  Orders other than 2 and 6: LBM_ERR_UNSUPPORTED. */
+LBM_API lbm_status lbm_set_hermite_orders(lbm_ctx* ctx, int eq_order, int force_order);
+
 /* Sets f = f^eq(rho, u), the complete (sixth-order Hermite) equilibrium of Eq. eq:truncation,
  * on every fluid node (rest state on solid nodes).  Arrays: N floats each, host or device.
  * Resets the step counter to 0. */
@@ -149,6 +161,14 @@ LBM_API lbm_status lbm_stream_only(lbm_ctx* ctx, int nsteps);
 LBM_API size_t lbm_halo_bytes(const lbm_ctx* ctx);
 LBM_API lbm_status lbm_halo_pack(lbm_ctx* ctx, int face, int stage, void* buf);
 LBM_API lbm_status lbm_halo_unpack(lbm_ctx* ctx, int face, int stage, const void* buf);
+/* Checkpoint / resume.  lbm_save writes a header (grid, storage, boundaries, nu, rho0, force,
+ * step counter, AA parity) and the raw population store to path; lbm_load reads it back into a
+ * context created with the same grid, storage and boundaries (LBM_ERR_STATE otherwise) and
+ * restores the step counter and parity, so that a resumed run continues bit for bit.  Force
+ * fields and masks are not saved: set them again on the new context.  Both wait for the stream. */
+LBM_API lbm_status lbm_save(lbm_ctx* ctx, const char* path);
+LBM_API lbm_status lbm_load(lbm_ctx* ctx, const char* path);
+
 /* Storage parity: 0 after an odd step or a set call (natural order), 1 after an even step. */
 LBM_API int lbm_parity(const lbm_ctx* ctx);
 
@@ -170,9 +190,10 @@ LBM_API lbm_status lbm_stats(lbm_ctx* ctx, double* out);
 LBM_API lbm_status lbm_synchronize(lbm_ctx* ctx);
 
 /* Kernel timing hook for benchmarks: with every >= 1, lbm_step records a CUDA event pair on the
- * context's stream around the stream-collide launch and the psi launch of every every-th step
- * (every = 0 turns it off).  It changes no result; the cost is two event records per timed
- * launch. */
+ * context's stream around the stream-collide launch and the psi launch of the steps t with
+ * t mod every in {0, 1} -- a pair of consecutive steps, so both AA parities (whose kernels differ)
+ * are sampled equally; every = 1 times all steps, every = 0 turns it off.  It changes no result;
+ * the cost is two event records per timed launch. */
 LBM_API lbm_status lbm_profile(lbm_ctx* ctx, int every);
 
 #define LBM_PROFILE_LEN 4
@@ -212,8 +233,9 @@ typedef struct {
 LBM_API lbm_status lbm_batch_create(const lbm_domain* domains, int count, double rho0, void* stream, lbm_batch** out);
 
 /* Times trial_steps (rounded to even, >= 2) graph-replayed steps for each candidate launch shape
- * (64, 128, 256 nodes per tile; 1/2x, 1x, 4x the resident blocks per SM) and keeps the fastest.
- * out (optional, 3 doubles): best MLUPS, nodes per tile, blocks per SM.  The trials advance the
+ * (64, 128, 256 nodes per tile; 1/2x, 1x, 4x the resident blocks per SM, or one block per tile)
+ * and keeps the fastest.  out (optional, 3 doubles): best MLUPS, nodes per tile, blocks per SM
+ * (0: one block per tile).  The trials advance the
  * state, so afterwards every domain is reset to rest: call it before lbm_batch_set_state. */
 LBM_API lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, double* out);
 

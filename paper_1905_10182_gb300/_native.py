@@ -72,6 +72,8 @@ def lib():
         L.lbm_create.restype = st
         L.lbm_set_force.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P, _P, _P]
         L.lbm_set_force.restype = st
+        L.lbm_set_hermite_orders.argtypes = [_P, ctypes.c_int, ctypes.c_int]
+        L.lbm_set_hermite_orders.restype = st
         L.lbm_set_state.argtypes = [_P, _P, _P, _P, _P]
         L.lbm_set_state.restype = st
         L.lbm_set_populations.argtypes = [_P, _P]
@@ -151,6 +153,10 @@ def lib():
         L.lbm_halo_pack.restype = st
         L.lbm_halo_unpack.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P]
         L.lbm_halo_unpack.restype = st
+        L.lbm_save.argtypes = [_P, ctypes.c_char_p]
+        L.lbm_save.restype = st
+        L.lbm_load.argtypes = [_P, ctypes.c_char_p]
+        L.lbm_load.restype = st
         L.lbm_parity.argtypes = [_P]
         L.lbm_parity.restype = ctypes.c_int
         L.lbm_time.argtypes = [_P]

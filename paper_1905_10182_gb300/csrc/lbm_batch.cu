@@ -300,16 +300,19 @@ cudaError_t launch_batch_step(lbm_batch* b, int odd) {
     return cudaGetLastError();
 }
 
+// blocks_per_sm = 0: one block per tile (the grid covers the tile list at this time; later
+// retirements only shorten the list, so the grid stays large enough).
 lbm_status set_shape(lbm_batch* b, int threads, int blocks_per_sm) {
     b->threads = threads;
     b->blocks_per_sm = blocks_per_sm;
-    b->grid = b->sms * blocks_per_sm;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
     b->graph_steps = 0;
-    return rebuild_tiles(b);
+    const lbm_status st = rebuild_tiles(b);
+    b->grid = blocks_per_sm > 0 ? b->sms * blocks_per_sm : std::max(1, b->ntiles);
+    return st;
 }
 
 // Captures `steps` (even) steps starting at even parity into a graph.
@@ -503,8 +506,9 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, double* out) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_step<true>, threads_c[ti], 0);
         if (e != cudaSuccess) return bcuda(b, e, "occupancy query");
         if (occ < 1) continue;
-        const int cand_b[3] = {occ, std::max(1, occ / 2), occ * 4};  // persistent, half, oversubscribed
-        for (int bi = 0; bi < 3; ++bi) {
+        // persistent, half, oversubscribed, one block per tile
+        const int cand_b[4] = {occ, std::max(1, occ / 2), occ * 4, 0};
+        for (int bi = 0; bi < 4; ++bi) {
             lbm_status st = set_shape(b, threads_c[ti], cand_b[bi]);
             if (st) return st;
             st = ensure_graph(b, trial_steps);

@@ -35,6 +35,7 @@ struct lbm_ctx {
     int force_kind = LBM_FORCE_NONE;
     float F[3] = {0, 0, 0};
     float G = 0;
+    int eq_order = 6, force_order = 6;  // Hermite truncation orders (6, 6): M1; (6, 2): M4; (2, 2): M5
     float* kolm = nullptr;  // ny entries
     float* field = nullptr; // 3N
     float* psi = nullptr;   // N
@@ -124,6 +125,9 @@ KParams make_params(const lbm_ctx* c) {
     p.flag = c->flag_dev;
     p.z0 = c->slab;
     p.local_off = (long long)c->slab * c->nx * c->ny;
+    p.ce = c->eq_order == 2 ? 1.0f : 0.0f;
+    p.cf = c->force_order == 2 ? 0.5f : 0.0f;
+    p.ho = (c->eq_order == 2 || c->force_order == 2) ? 1 : 0;
     return p;
 }
 
@@ -220,7 +224,8 @@ lbm_status run_macro(lbm_ctx* c) {
 
 // Records one event of a timing pair when profiling is on.
 lbm_status profile_mark(lbm_ctx* c, int kind) {
-    if (c->profile <= 0 || (c->t % c->profile) != 0) return LBM_OK;
+    // the step pair t = 0, 1 (mod every): both AA parities, whose kernels differ
+    if (c->profile <= 0 || (c->profile > 1 && (c->t % c->profile) > 1)) return LBM_OK;
     if (c->events_used == c->events.size()) {
         cudaEvent_t e;
         CK(c, cudaEventCreate(&e), "cudaEventCreate");
@@ -243,7 +248,7 @@ lbm_status do_steps(lbm_ctx* c, int nsteps, bool trace) {
             if ((st = profile_mark(c, 1))) return st;
         }
         if ((st = profile_mark(c, 0))) return st;
-        CK(c, DISPATCH(c, launch_step, p, c->f, c->parity, fk, trace ? 1 : 0, c->stream), "stream-collide kernel");
+        CK(c, DISPATCH(c, launch_step, p, c->f, c->parity, fk, trace ? 1 : 0, p.ho, c->stream), "stream-collide kernel");
         if ((st = profile_mark(c, 0))) return st;
         c->parity ^= 1;
         ++c->t;
@@ -394,6 +399,15 @@ lbm_status lbm_set_force(lbm_ctx* c, int kind, const double* params, const float
         return fail(c, LBM_ERR_ARG, "unknown force kind");
     }
     c->force_kind = kind;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_hermite_orders(lbm_ctx* c, int eq_order, int force_order) {
+    if (!c) return LBM_ERR_ARG;
+    if ((eq_order != 2 && eq_order != 6) || (force_order != 2 && force_order != 6))
+        return fail(c, LBM_ERR_UNSUPPORTED, "Hermite orders must be 2 or 6");
+    c->eq_order = eq_order;
+    c->force_order = force_order;
     return LBM_OK;
 }
 
@@ -574,6 +588,73 @@ lbm_status lbm_halo_unpack(lbm_ctx* c, int face, int stage, const void* buf) {
 }
 
 int lbm_parity(const lbm_ctx* c) { return c ? c->parity : -1; }
+
+// Checkpoint file: a fixed header, then the raw population store (storage type, AA order as is).
+struct CkptHeader {
+    char magic[8];
+    int32_t version, nx, ny, nz, storage, slab, walls_y, parity;
+    int64_t t;
+    double nu, rho0;
+    int32_t force_kind, eq_order, force_order;
+    float F[3], G;
+    uint64_t store_bytes;
+};
+
+lbm_status lbm_save(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_ERR_ARG;
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "CMLBMCK1", 8);
+    h.version = 1;
+    h.nx = c->nx;
+    h.ny = c->ny;
+    h.nz = c->nz;
+    h.storage = c->storage;
+    h.slab = c->slab;
+    h.walls_y = c->walls_y;
+    h.parity = c->parity;
+    h.t = c->t;
+    h.nu = c->nu;
+    h.rho0 = c->rho0;
+    h.force_kind = c->force_kind;
+    h.eq_order = c->eq_order;
+    h.force_order = c->force_order;
+    std::memcpy(h.F, c->F, sizeof(h.F));
+    h.G = c->G;
+    h.store_bytes = (uint64_t)27 * (uint64_t)c->N * elem_size(c->storage);
+    std::vector<char> buf(h.store_bytes);
+    CK(c, cudaMemcpyAsync(buf.data(), c->f, h.store_bytes, cudaMemcpyDeviceToHost, c->stream), "checkpoint copy");
+    CK(c, cudaStreamSynchronize(c->stream), "checkpoint sync");
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(c, LBM_ERR_ARG, std::string("cannot open ") + path);
+    const bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 && std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    std::fclose(fp);
+    if (!ok) return fail(c, LBM_ERR_ARG, std::string("short write to ") + path);
+    return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_ERR_ARG;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(c, LBM_ERR_ARG, std::string("cannot open ") + path);
+    CkptHeader h;
+    bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::memcmp(h.magic, "CMLBMCK1", 8) == 0 && h.version == 1;
+    if (ok && (h.nx != c->nx || h.ny != c->ny || h.nz != c->nz || h.storage != c->storage || h.slab != c->slab ||
+               h.walls_y != c->walls_y || h.store_bytes != (uint64_t)27 * (uint64_t)c->N * elem_size(c->storage))) {
+        std::fclose(fp);
+        return fail(c, LBM_ERR_STATE, "checkpoint grid, storage or boundaries differ from the context");
+    }
+    std::vector<char> buf(ok ? h.store_bytes : 0);
+    if (ok) ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
+    std::fclose(fp);
+    if (!ok) return fail(c, LBM_ERR_ARG, std::string("not a complete checkpoint: ") + path);
+    CK(c, cudaMemcpyAsync(c->f, buf.data(), h.store_bytes, cudaMemcpyHostToDevice, c->stream), "checkpoint copy");
+    CK(c, cudaStreamSynchronize(c->stream), "checkpoint sync");
+    c->parity = h.parity;
+    c->t = h.t;
+    c->have_uprev = false;
+    return LBM_OK;
+}
 
 lbm_status lbm_profile(lbm_ctx* c, int every) {
     if (!c) return LBM_ERR_ARG;

@@ -79,6 +79,8 @@ struct KParams {
     unsigned int* flag;    // set to 1 when a node has rho <= 0, |u| >= 1 or a NaN
     int z0;                // first active plane of the store (1 for a z slab with ghost planes, else 0)
     long long local_off;   // z0 * nx * ny: store node index minus caller (local) node index
+    int ho;                // 1: second-order Hermite truncation of f^eq and/or F_i (models M4, M5)
+    float ce, cf;          // weights of hermite2_correction (1 / 0 and 1/2 / 0)
 };
 
 // Node coordinates and the offsets of its 26 neighbours with periodic wrap in x, y, z.
@@ -290,10 +292,73 @@ __device__ __forceinline__ void d1q3_inverse_lin(float m0, float m1, float m2, f
     pm = 0.5f * (t - a);
 }
 
+// Models with second-order Hermite truncations (Sec. III: M4 keeps the complete equilibrium with
+// the second-order (Guo) forcing term, M5 truncates both at second order).  For any truncation
+// order >= 2 the central moments of order <= 2 of f^eq and of F_i are those of the complete
+// expansion (the D3Q27 quadrature is exact there), so the five omega-relaxed moments k4..k8 are
+// untouched and only the moments of order >= 3, all relaxed at rate 1 (k* = k^eq + R/2), change.
+// Adds to the monomial post-collision central moments K[a][b][c] (x, y, z orders):
+//   ce * (kappa^eq of the 2nd-order equilibrium - kappa^eq of the complete one)
+// + cf * (kappa of the 2nd-order forcing term - kappa of the complete one),
+// ce = 1 for a second-order equilibrium, cf = 1/2 for a second-order forcing term, else 0.
+// The differences are the central moments of the dropped Hermite terms H^(3)..H^(6) of
+// Eq. eq:truncation and Eq. generalForcing, expanded about u.
+// T: float (one node) or a packed pair of nodes with the same arithmetic operators.
+template <typename T>
+__device__ __forceinline__ void hermite2_correction(T (&K)[3][3][3], T rho, T ux, T uy, T uz, T Fx, T Fy, T Fz,
+                                                    float ce, float cf) {
+    const T re = ce * rho;
+    const T X = ux * ux, Y = uy * uy, Z = uz * uz;
+    // third order, kappa with u_a squared and u_b: -rho u_a^2 u_b; -u_a (2 F_a u_b + F_b u_a)
+    auto t3 = [&](T ua, T ub, T Fa, T Fb) {
+        return -re * ua * ua * ub - cf * ua * (2.0f * Fa * ub + Fb * ua);
+    };
+    K[2][1][0] += t3(ux, uy, Fx, Fy);
+    K[2][0][1] += t3(ux, uz, Fx, Fz);
+    K[1][2][0] += t3(uy, ux, Fy, Fx);
+    K[0][2][1] += t3(uy, uz, Fy, Fz);
+    K[1][0][2] += t3(uz, ux, Fz, Fx);
+    K[0][1][2] += t3(uz, uy, Fz, Fy);
+    K[1][1][1] += -re * ux * uy * uz - cf * (Fx * uy * uz + Fy * ux * uz + Fz * ux * uy);
+    // fourth order, a^2 b^2: 3 rho u_a^2 u_b^2; 4 u_a u_b (F_a u_b + F_b u_a)
+    auto t4 = [&](T ua, T ub, T Fa, T Fb) {
+        return 3.0f * re * ua * ua * ub * ub + 4.0f * cf * ua * ub * (Fa * ub + Fb * ua);
+    };
+    K[2][2][0] += t4(ux, uy, Fx, Fy);
+    K[2][0][2] += t4(ux, uz, Fx, Fz);
+    K[0][2][2] += t4(uy, uz, Fy, Fz);
+    // fourth order, a^2 b c: 3 rho u_a^2 u_b u_c; 2 u_a (2 F_a u_b u_c + F_b u_a u_c + F_c u_a u_b)
+    auto t4m = [&](T ua, T ub, T uc, T Fa, T Fb, T Fc) {
+        return 3.0f * re * ua * ua * ub * uc + 2.0f * cf * ua * (2.0f * Fa * ub * uc + Fb * ua * uc + Fc * ua * ub);
+    };
+    K[2][1][1] += t4m(ux, uy, uz, Fx, Fy, Fz);
+    K[1][2][1] += t4m(uy, ux, uz, Fy, Fx, Fz);
+    K[1][1][2] += t4m(uz, ux, uy, Fz, Fx, Fy);
+    // fifth order, a b^2 c^2: -rho u_a (18 u_b^2 u_c^2 + u_b^2 + u_c^2) / 3;
+    // -(F_a (9 u_b^2 u_c^2 + u_b^2 + u_c^2) + 2 u_a (F_b u_b (9 u_c^2 + 1) + F_c u_c (9 u_b^2 + 1))) / 3
+    auto t5 = [&](T ua, T ub, T uc, T Fa, T Fb, T Fc) {
+        const T b2 = ub * ub, c2 = uc * uc;
+        return -(re * ua * (18.0f * b2 * c2 + b2 + c2) +
+                 cf * (Fa * (9.0f * b2 * c2 + b2 + c2) +
+                       2.0f * ua * (Fb * ub * (9.0f * c2 + 1.0f) + Fc * uc * (9.0f * b2 + 1.0f)))) *
+               (1.0f / 3.0f);
+    };
+    K[1][2][2] += t5(ux, uy, uz, Fx, Fy, Fz);
+    K[2][1][2] += t5(uy, ux, uz, Fy, Fx, Fz);
+    K[2][2][1] += t5(uz, ux, uy, Fz, Fx, Fy);
+    // sixth order: rho (10 X Y Z + X Y + X Z + Y Z); (4/3) sum_a F_a u_a (6 u_b^2 u_c^2 + u_b^2 + u_c^2)
+    K[2][2][2] += re * (10.0f * X * Y * Z + X * Y + X * Z + Y * Z) +
+                  cf * (4.0f / 3.0f) *
+                      (Fx * ux * (6.0f * Y * Z + Y + Z) + Fy * uy * (6.0f * X * Z + X + Z) +
+                       Fz * uz * (6.0f * X * Y + X + Y));
+}
+
 // In: K[x][y][z] holds the deviations g arranged by velocity (index c + 1).  Out: K holds the
-// increments dg arranged the same way.  Returns rho and u of the node.
+// increments dg arranged the same way.  Returns rho and u of the node.  HO: add the
+// second-order-truncation terms of hermite2_correction (weights ce, cf).
+template <bool HO = false>
 __device__ __forceinline__ Macro collide_increment(float (&K)[3][3][3], float Fx, float Fy, float Fz, float omega,
-                                                   float rho0) {
+                                                   float rho0, float ce = 0.0f, float cf = 0.0f) {
     constexpr float s[3] = {1.0f, 0.0f, 1.0f / 3.0f};
 
     // raw moments of the deviations: z, then y, then x (index: [x][y][z], each either a velocity
@@ -370,6 +435,7 @@ __device__ __forceinline__ Macro collide_increment(float (&K)[3][3][3], float Fx
     K[2][1][2] = Fy * (1.0f / 18.0f) - K[2][1][2];
     K[2][2][1] = Fz * (1.0f / 18.0f) - K[2][2][1];
     K[2][2][2] = dr * (1.0f / 27.0f) - K[2][2][2];
+    if (HO) hermite2_correction(K, rho, ux, uy, uz, Fx, Fy, Fz, ce, cf);
 
     // step 4: dg = (T^T)^-1 dk, z then y then x inverses; g* = g + dg
     const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
@@ -391,11 +457,13 @@ __device__ __forceinline__ Macro collide_increment(float (&K)[3][3][3], float Fx
     return Macro{rho, ux, uy, uz};
 }
 
-__device__ __forceinline__ Macro collide_cm(float (&g)[27], float Fx, float Fy, float Fz, float omega, float rho0) {
+template <bool HO = false>
+__device__ __forceinline__ Macro collide_cm(float (&g)[27], float Fx, float Fy, float Fz, float omega, float rho0,
+                                            float ce = 0.0f, float cf = 0.0f) {
     float K[3][3][3];
 #pragma unroll
     for (int i = 0; i < 27; ++i) K[dir_x(i) + 1][dir_y(i) + 1][dir_z(i) + 1] = g[i];
-    const Macro m = collide_increment(K, Fx, Fy, Fz, omega, rho0);
+    const Macro m = collide_increment<HO>(K, Fx, Fy, Fz, omega, rho0, ce, cf);
 #pragma unroll
     for (int i = 0; i < 27; ++i) g[i] += K[dir_x(i) + 1][dir_y(i) + 1][dir_z(i) + 1];
     return m;
@@ -405,8 +473,9 @@ __device__ __forceinline__ Macro collide_cm(float (&g)[27], float Fx, float Fy, 
 // Eq. post_collision_central_moments_forcing, used with 16-bit storage: it needs only the ten raw
 // moments of order <= 2 and one inverse transform, and its FP32 rounding (a few ulp of |g| per
 // step) stays far below the 2^-11 / 2^-8 rounding of FP16 / BF16 storage.
+template <bool HO = false>
 __device__ __forceinline__ Macro collide_cm_direct(float (&g)[27], float Fx, float Fy, float Fz, float omega,
-                                                   float rho0) {
+                                                   float rho0, float ce = 0.0f, float cf = 0.0f) {
     const RawMoments m = raw_moments(g);
     const float dr = m.m000;
     const float rho = rho0 + dr;
@@ -444,6 +513,7 @@ __device__ __forceinline__ Macro collide_cm_direct(float (&g)[27], float Fx, flo
     kd[2][1][2] = Fy * (1.0f / 18.0f);
     kd[2][2][1] = Fz * (1.0f / 18.0f);
     kd[2][2][2] = dr * (1.0f / 27.0f);
+    if (HO) hermite2_correction(kd, rho, ux, uy, uz, Fx, Fy, Fz, ce, cf);
     inverse_fast_dev(kd, ux, uy, uz, rho0, g);
     return Macro{rho, ux, uy, uz};
 }

@@ -1,3 +1,3 @@
 // Kernel instantiation, float population storage: odd-parity step.
 #include "lbm_kernels.cuh"
-CMLBM_INSTANTIATE_STEP(float, true)
+CMLBM_INSTANTIATE_STEP(float, true, false)

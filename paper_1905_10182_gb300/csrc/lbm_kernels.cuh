@@ -7,6 +7,7 @@
 
 #include "lbm_device.cuh"
 #include "lbm_launch.h"
+#include "lbm_x2.cuh"
 
 namespace cmlbm {
 
@@ -23,44 +24,11 @@ __device__ __forceinline__ void check_node(const KParams& p, const Macro& m) {
 
 // K1: one fused AA stream-collide step.  TRACE replaces the collision by the identity, which
 // turns the step into pure streaming with bounce-back (used to check indices bit-exactly).
-// Shan-Chen stencil from a shared-memory tile: the block's row segment of psi with one node of
-// x halo, for the 3 x 3 rows (y - 1 .. y + 1, z - 1 .. z + 1) around it.
-__device__ __forceinline__ void sc_force_tile(const KParams& p, const float (*tile)[BLOCK_X + 2], int t, float& Fx,
-                                              float& Fy, float& Fz) {
-    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-#pragma unroll
-    for (int i = 1; i < 27; ++i) {
-        const float v = tile[(dir_z(i) + 1) * 3 + dir_y(i) + 1][t + 1 + dir_x(i)];
-        if (dir_x(i)) sx = fmaf(dir_x(i) > 0 ? weight(i) : -weight(i), v, sx);
-        if (dir_y(i)) sy = fmaf(dir_y(i) > 0 ? weight(i) : -weight(i), v, sy);
-        if (dir_z(i)) sz = fmaf(dir_z(i) > 0 ? weight(i) : -weight(i), v, sz);
-    }
-    const float a = -p.G * tile[4][t + 1];
-    Fx = a * sx;
-    Fy = a * sy;
-    Fz = a * sz;
-}
-
-template <typename S, bool ODD, bool LINKS, int FK, bool TRACE>
+// HO: the second-order Hermite truncations (models M4, M5 of Sec. III) instead of the complete ones.
+template <typename S, bool ODD, bool LINKS, int FK, bool TRACE, bool HO>
 __global__ void __launch_bounds__(BLOCK_X, (sizeof(S) == 4 ? 4 : 5)) k_stream_collide(KParams p, S* __restrict__ f) {
     const int x = blockIdx.x * BLOCK_X + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z + p.z0;
-    // Shan-Chen: stage the psi rows of the stencil once per block (before any thread leaves)
-    __shared__ float psi_tile[(FK == FK_SHAN_CHEN && !TRACE) ? 9 : 1][BLOCK_X + 2];
-    if constexpr (FK == FK_SHAN_CHEN && !TRACE) {
-        const int x0 = blockIdx.x * BLOCK_X;
-        const uint32_t nx = p.nx, ny = p.ny, nz = p.nz;
-        for (int k = threadIdx.x; k < 9 * (BLOCK_X + 2); k += BLOCK_X) {
-            const int r = k / (BLOCK_X + 2), c = k % (BLOCK_X + 2);
-            const int xx = x0 + c - 1;
-            if (xx > (int)nx) continue;  // beyond the row end and its halo node
-            const uint32_t xw = xx < 0 ? nx - 1 : (xx >= (int)nx ? 0 : (uint32_t)xx);
-            const int dy = r % 3 - 1, dz = r / 3 - 1;
-            const uint32_t yw = (uint32_t)((y + dy + (int)ny) % (int)ny), zw = (uint32_t)((z + dz + (int)nz) % (int)nz);
-            psi_tile[r][c] = p.psi[xw + nx * (yw + ny * zw)];
-        }
-        __syncthreads();
-    }
     if (x >= p.nx) return;
     const Nbr nb(x, y, z, p);
     uint32_t link = 0;
@@ -72,26 +40,26 @@ __global__ void __launch_bounds__(BLOCK_X, (sizeof(S) == 4 ? 4 : 5)) k_stream_co
     aa_gather<S, ODD, LINKS>(f, p.N, nb, link, g);
     if (!TRACE) {
         float Fx, Fy, Fz;
-        if constexpr (FK == FK_SHAN_CHEN)
-            sc_force_tile(p, psi_tile, threadIdx.x, Fx, Fy, Fz);
-        else
-            node_force<FK>(p, nb, y, Fx, Fy, Fz);
+        node_force<FK>(p, nb, y, Fx, Fy, Fz);
         // FP32 storage: increment form (rounding scales with the change); 16-bit: direct form
         Macro m;
         if constexpr (sizeof(S) == 4)
-            m = collide_cm(g, Fx, Fy, Fz, p.omega, p.rho0);
+            m = collide_cm<HO>(g, Fx, Fy, Fz, p.omega, p.rho0, p.ce, p.cf);
         else
-            m = collide_cm_direct(g, Fx, Fy, Fz, p.omega, p.rho0);
+            m = collide_cm_direct<HO>(g, Fx, Fy, Fz, p.omega, p.rho0, p.ce, p.cf);
         check_node(p, m);
     }
     aa_scatter<S, ODD, LINKS>(f, p.N, nb, link, g);
 }
 
 // K3: psi = 1 - exp(-rho) of every node at the current time (the Shan-Chen pseudo-potential).
+// Blocks walk the grid in reverse order: this pass starts where the preceding stream-collide
+// pass ended and ends where the next one starts, so both hand-overs find the most recently
+// touched part of the store (up to the 129 MB of L2) still in L2.
 template <typename S, bool ODD, bool LINKS>
 __global__ void __launch_bounds__(BLOCK_X) k_psi(KParams p, const S* __restrict__ f, float* __restrict__ psi) {
-    const int x = blockIdx.x * BLOCK_X + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z + p.z0;
+    const int x = (gridDim.x - 1 - blockIdx.x) * BLOCK_X + threadIdx.x;
+    const int y = gridDim.y - 1 - blockIdx.y, z = gridDim.z - 1 - blockIdx.z + p.z0;
     if (x >= p.nx) return;
     const Nbr nb(x, y, z, p);
     uint32_t link = 0;
@@ -194,32 +162,48 @@ static inline dim3 node_grid(const KParams& p) {
 }
 
 // ----------------------------------------------------------------------------- launchers
-template <typename S, bool ODD, bool LINKS>
+template <typename S, bool ODD, bool LINKS, bool HO>
 static cudaError_t launch_step_t(const KParams& p, S* f, int fk, bool trace, cudaStream_t st) {
     const dim3 grid = node_grid(p), block(BLOCK_X);
+    if constexpr (sizeof(S) == 2 && !LINKS) {
+        // 16-bit storage, fully periodic, even nx, 4-byte aligned store: two nodes per thread
+        if (!trace && p.nx % 2 == 0 && (reinterpret_cast<uintptr_t>(f) & 3) == 0) {
+            const uint32_t np = p.nx / 2, per = x2_pairs_per_block<ODD>(), per_sc = x2_pairs_per_block<true>();
+            const dim3 grid2((np + per - 1) / per, p.ny, p.nz - 2 * p.z0);
+            const dim3 grid_sc((np + per_sc - 1) / per_sc, p.ny, p.nz - 2 * p.z0);
+            switch (fk) {
+            case FK_CONST: k_stream_collide_x2<S, ODD, FK_CONST, HO><<<grid2, X2_BLOCK, 0, st>>>(p, f); break;
+            case FK_KOLMOGOROV: k_stream_collide_x2<S, ODD, FK_KOLMOGOROV, HO><<<grid2, X2_BLOCK, 0, st>>>(p, f); break;
+            case FK_FIELD: k_stream_collide_x2<S, ODD, FK_FIELD, HO><<<grid2, X2_BLOCK, 0, st>>>(p, f); break;
+            case FK_SHAN_CHEN: k_stream_collide_x2<S, ODD, FK_SHAN_CHEN, HO><<<grid_sc, X2_BLOCK, 0, st>>>(p, f); break;
+            default: return cudaErrorInvalidValue;
+            }
+            return cudaGetLastError();
+        }
+    }
     if (trace) {
         // free streaming is only offered for FP32 storage (bit-exact index checks)
-        if constexpr (std::is_same<S, float>::value)
-            k_stream_collide<S, ODD, LINKS, FK_CONST, true><<<grid, block, 0, st>>>(p, f);
+        if constexpr (std::is_same<S, float>::value && !HO)
+            k_stream_collide<S, ODD, LINKS, FK_CONST, true, false><<<grid, block, 0, st>>>(p, f);
         else
             return cudaErrorInvalidValue;
     } else {
         switch (fk) {
-        case FK_CONST: k_stream_collide<S, ODD, LINKS, FK_CONST, false><<<grid, block, 0, st>>>(p, f); break;
-        case FK_KOLMOGOROV: k_stream_collide<S, ODD, LINKS, FK_KOLMOGOROV, false><<<grid, block, 0, st>>>(p, f); break;
-        case FK_FIELD: k_stream_collide<S, ODD, LINKS, FK_FIELD, false><<<grid, block, 0, st>>>(p, f); break;
-        case FK_SHAN_CHEN: k_stream_collide<S, ODD, LINKS, FK_SHAN_CHEN, false><<<grid, block, 0, st>>>(p, f); break;
+        case FK_CONST: k_stream_collide<S, ODD, LINKS, FK_CONST, false, HO><<<grid, block, 0, st>>>(p, f); break;
+        case FK_KOLMOGOROV: k_stream_collide<S, ODD, LINKS, FK_KOLMOGOROV, false, HO><<<grid, block, 0, st>>>(p, f); break;
+        case FK_FIELD: k_stream_collide<S, ODD, LINKS, FK_FIELD, false, HO><<<grid, block, 0, st>>>(p, f); break;
+        case FK_SHAN_CHEN: k_stream_collide<S, ODD, LINKS, FK_SHAN_CHEN, false, HO><<<grid, block, 0, st>>>(p, f); break;
         default: return cudaErrorInvalidValue;
         }
     }
     return cudaGetLastError();
 }
 
-template <typename S, bool ODD>
+template <typename S, bool ODD, bool HO>
 cudaError_t launch_step_parity(const KParams& p, void* f, int fk, int trace, cudaStream_t st) {
     S* fs = static_cast<S*>(f);
-    return p.links != nullptr ? launch_step_t<S, ODD, true>(p, fs, fk, trace != 0, st)
-                              : launch_step_t<S, ODD, false>(p, fs, fk, trace != 0, st);
+    return p.links != nullptr ? launch_step_t<S, ODD, true, HO>(p, fs, fk, trace != 0, st)
+                              : launch_step_t<S, ODD, false, HO>(p, fs, fk, trace != 0, st);
 }
 
 template <typename S>
@@ -323,9 +307,9 @@ cudaError_t launch_init_equilibrium(const KParams& p, void* f, const float* rho,
 
 }  // namespace cmlbm
 
-#define CMLBM_INSTANTIATE_STEP(S, ODD)                                                                          \
+#define CMLBM_INSTANTIATE_STEP(S, ODD, HO)                                                                      \
     namespace cmlbm {                                                                                            \
-    template cudaError_t launch_step_parity<S, ODD>(const KParams&, void*, int, int, cudaStream_t);              \
+    template cudaError_t launch_step_parity<S, ODD, HO>(const KParams&, void*, int, int, cudaStream_t);          \
     }
 
 #define CMLBM_INSTANTIATE_MISC(S)                                                                                 \

@@ -1,5 +1,5 @@
 // Host-side launch interface between the C-ABI (lbm_capi.cu) and the kernels, which are
-// instantiated once per storage type in lbm_kernels_{f32,f16,bf16}.cu.
+// instantiated per storage type and step parity in lbm_k_{f32,f16,bf16}_{even,odd}.cu.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -8,11 +8,16 @@ namespace cmlbm {
 
 struct KParams;
 
-template <typename S, bool ODD>
+template <typename S, bool ODD, bool HO>
 cudaError_t launch_step_parity(const KParams& p, void* f, int fk, int trace, cudaStream_t st);
+// ho: the second-order Hermite truncation variants (instantiated in lbm_k_*_ho_*.cu)
 template <typename S>
-inline cudaError_t launch_step(const KParams& p, void* f, int odd, int fk, int trace, cudaStream_t st) {
-    return odd ? launch_step_parity<S, true>(p, f, fk, trace, st) : launch_step_parity<S, false>(p, f, fk, trace, st);
+inline cudaError_t launch_step(const KParams& p, void* f, int odd, int fk, int trace, int ho, cudaStream_t st) {
+    if (ho)
+        return odd ? launch_step_parity<S, true, true>(p, f, fk, trace, st)
+                   : launch_step_parity<S, false, true>(p, f, fk, trace, st);
+    return odd ? launch_step_parity<S, true, false>(p, f, fk, trace, st)
+               : launch_step_parity<S, false, false>(p, f, fk, trace, st);
 }
 template <typename S>
 cudaError_t launch_psi(const KParams& p, const void* f, float* psi, int odd, cudaStream_t st);

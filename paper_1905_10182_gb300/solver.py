@@ -98,6 +98,16 @@ class Solver:
         self._keep = [_f32(fx), _f32(fy), _f32(fz)]
         self._check(self._lib.lbm_set_force(self._h, k, par, *(nat.ptr(a) for a in self._keep)))
 
+    # Hermite truncation orders (equilibrium, forcing) of the models compared in Sec. III
+    MODELS = {"M1": (6, 6), "M4": (6, 2), "M5": (2, 2)}
+
+    def set_hermite_orders(self, eq_order, force_order):
+        self._check(self._lib.lbm_set_hermite_orders(self._h, int(eq_order), int(force_order)))
+
+    def set_model(self, name):
+        """'M1' (complete expansions, default), 'M4' (Guo forcing) or 'M5' (second-order both)."""
+        self.set_hermite_orders(*self.MODELS[name])
+
     def set_state(self, rho, ux, uy, uz):
         arrs = [_f32(a) for a in (rho, ux, uy, uz)]
         self._check(self._lib.lbm_set_state(self._h, *(nat.ptr(a) for a in arrs)))
@@ -131,6 +141,12 @@ class Solver:
         keys = ("mass", "mom_x", "mom_y", "mom_z", "residual", "kinetic_energy", "enstrophy", "umax",
                 "fluid_nodes", "step")
         return dict(zip(keys, list(out)))
+
+    def save(self, path):
+        self._check(self._lib.lbm_save(self._h, str(path).encode()))
+
+    def load(self, path):
+        self._check(self._lib.lbm_load(self._h, str(path).encode()))
 
     # -- z slabs (see paper_1905_10182_gb300.slabs)
     @property

@@ -88,7 +88,8 @@ def test_batch_autotune_resets_to_rest():
     doms = _domains()
     b = BatchSolver(doms)
     out = b.autotune(trial_steps=4)
-    assert out["tile"] in (64, 128, 256) and out["blocks_per_sm"] >= 1 and out["mlups"] > 0
+    # blocks_per_sm = 0: one block per tile
+    assert out["tile"] in (64, 128, 256) and out["blocks_per_sm"] >= 0 and out["mlups"] > 0
     assert b.time == 0
     for k in range(len(doms)):
         assert np.abs(b.get_populations(k)).max() == 0.0

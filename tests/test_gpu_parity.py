@@ -48,8 +48,8 @@ def scale(orc, f, og=None):
 RAGGED = (19, 13, 11)  # several 128-wide x tiles are not needed: ragged in every axis
 
 
-def _case(name, orc):
-    nx, ny, nz = RAGGED
+def _case(name, orc, shape=RAGGED):
+    nx, ny, nz = shape
     g = inputs.random_deviations(nx, ny, nz, seed=1)
     kw = dict(nu=0.07)
     okw = dict(nu=0.07)
@@ -311,3 +311,162 @@ def test_device_and_host_arguments_agree():
     ra, *_ = a.macroscopic()
     assert np.array_equal(ra, rho.cpu().numpy())
 
+
+
+@pytest.mark.parametrize("storage,odd", [("fp32", True), ("bf16", False)])
+def test_checkpoint_file_resume_bit_exact(tmp_path, storage, odd):
+    """2n steps equal n steps + lbm_save + lbm_load into a new context + n steps, bit for bit, also
+    when the checkpoint is taken at odd AA parity."""
+    nx, ny, nz = 23, 12, 7
+    g = inputs.random_deviations(nx, ny, nz, seed=16)
+    n = 5 if odd else 4
+    a = Solver(nx, ny, nz, nu=0.03, walls_y=True, storage=storage)
+    a.set_force("kolmogorov", (2e-5,))
+    a.set_populations(g)
+    a.step(2 * n)
+    b = Solver(nx, ny, nz, nu=0.03, walls_y=True, storage=storage)
+    b.set_force("kolmogorov", (2e-5,))
+    b.set_populations(g)
+    b.step(n)
+    b.save(tmp_path / "ck.bin")
+    c = Solver(nx, ny, nz, nu=0.03, walls_y=True, storage=storage)
+    c.set_force("kolmogorov", (2e-5,))
+    c.load(tmp_path / "ck.bin")
+    assert c.time == n
+    c.step(n)
+    assert np.array_equal(a.get_populations(), c.get_populations())
+    wrong = Solver(nx + 1, ny, nz, nu=0.03, walls_y=True, storage=storage)
+    with pytest.raises(LbmError):
+        wrong.load(tmp_path / "ck.bin")
+
+
+def _moving_state(orc, nx, ny, nz, seed, umax=0.1, drho=0.1):
+    """FP32 deviations of f^eq(rho, u) (oracle, FP64) with |u| up to umax plus 1e-3 noise: a state
+    where the velocity-dependent third- to sixth-order moments of the truncated models matter."""
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + drho * (rng.random((nz, ny, nx)) - 0.5)
+    u = umax * (2.0 * rng.random((3, nz, ny, nx)) - 1.0)
+    f = orc.Grid(nx, ny, nz, nu=0.1).init_equilibrium(rho, u)
+    return (dev(orc, f) + inputs.random_deviations(nx, ny, nz, seed=seed + 1)).astype(np.float32)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("orders", [(6, 2), (2, 2), (2, 6)], ids=["M4", "M5", "eq2"])
+@pytest.mark.parametrize("name", ["field", "walls_mask", "shan_chen"])
+def test_hermite_orders_match_oracle(orc, name, orders, storage):
+    """Second-order Hermite truncations of f^eq and/or F_i (models M4 and M5 of Sec. III) against
+    the oracle's literal collision (Eq. for k* with the truncated f^eq and F_i, solved with T^T),
+    1-3 steps from a state with |u| ~ 0.1.  The step bound is the one of test_steps_match_oracle;
+    the oracle's own M1 result must lie far outside it, so the case does exercise the terms."""
+    nx, ny, nz = RAGGED
+    eq, fo = orders
+    g = _moving_state(orc, nx, ny, nz, seed=21)
+    kw, okw = dict(nu=0.05), dict(nu=0.05, collision=orc.COLL_LITERAL)
+    if name == "field":
+        F = inputs.random_force_field(nx, ny, nz, seed=22, amp=5e-2)
+        force = ("field", None, F[0], F[1], F[2])
+        okw.update(force_kind=orc.FORCE_FIELD, field=F.astype(np.float64))
+    elif name == "walls_mask":
+        mask = inputs.random_mask(nx, ny, nz, seed=23, fraction=0.15)
+        kw.update(walls_y=True, mask=mask)
+        okw.update(walls_y=True, mask=mask, force_kind=orc.FORCE_UNIFORM, force=(5e-2, -2.5e-2, 1e-2))
+        force = ("uniform", (5e-2, -2.5e-2, 1e-2))
+    else:
+        kw.update(nu=0.1)
+        okw.update(nu=0.1, force_kind=orc.FORCE_SHAN_CHEN, G=-5.5)
+        force = ("shan_chen", (-5.5,))
+    s = Solver(nx, ny, nz, storage=storage, **kw)
+    s.set_force(*force)
+    s.set_hermite_orders(eq, fo)
+    s.set_populations(g)
+    og = orc.Grid(nx, ny, nz, eq_order=eq, force_order=fo, **okw)
+    o1 = orc.Grid(nx, ny, nz, **okw)  # complete expansions (M1)
+    f = full(orc, storage_round(g, storage))
+    S = scale(orc, f, og)
+    fluid = np.ones((nz, ny, nx), bool) if kw.get("mask") is None else kw["mask"] == 0
+    tol1 = C_STEP * EPS32 * S + half_ulp(np.abs(dev(orc, f)).max(), storage)
+    m1 = dev(orc, o1.step(f, 1))
+    for n in (1, 2, 3):
+        s.step(1)
+        f = og.step(f, 1)
+        ref = dev(orc, f)
+        if n == 1:
+            sep = np.abs(ref - m1)[:, fluid].max()
+            assert sep > 5 * tol1, (name, orders, storage, sep, tol1)
+        got = s.get_populations().astype(np.float64)
+        err = np.abs(got - ref)[:, fluid].max()
+        tol = n * (C_STEP * EPS32 * S + half_ulp(np.abs(ref).max(), storage))
+        assert err <= tol, (name, orders, storage, n, err, tol)
+
+
+def test_hermite_orders_rejected():
+    s = Solver(8, 8, 8, nu=0.1)
+    for bad in ((3, 6), (6, 4), (0, 0)):
+        with pytest.raises(LbmError):
+            s.set_hermite_orders(*bad)
+    s.set_model("M5")
+    s.set_model("M1")
+
+
+# Shapes that take the two-nodes-per-thread kernel (16-bit storage, periodic, even nx): one block;
+# a warp with a single pair after a full one; two blocks with a partial one; the smallest row.
+PAIR_SHAPES = [(20, 13, 11), (66, 5, 4), (300, 4, 3), (2, 5, 3)]
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("shape", PAIR_SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("name", ["periodic_uniform", "kolmogorov", "field", "shan_chen"])
+def test_pair_kernel_steps_match_oracle(orc, name, shape, storage):
+    """The 16-bit kernel that updates two nodes per thread (32-bit pair loads and stores, warp
+    shuffles for the x neighbours, wrap at the row ends) against the oracle, 1-3 steps (both AA
+    parities), with the bound of test_steps_match_oracle."""
+    g, kw, okw, force = _case(name, orc, shape)
+    nx, ny, nz = shape
+    s = Solver(nx, ny, nz, storage=storage, **kw)
+    if force:
+        s.set_force(*force)
+    s.set_populations(g)
+    og = orc.Grid(nx, ny, nz, collision=orc.COLL_PAPER, **okw)
+    f = full(orc, storage_round(g, storage))
+    S = scale(orc, f, og)
+    for n in (1, 2, 3):
+        s.step(1)
+        f = og.step(f, 1)
+        got = s.get_populations().astype(np.float64)
+        ref = dev(orc, f)
+        err = np.abs(got - ref).max()
+        tol = n * (C_STEP * EPS32 * S + half_ulp(np.abs(ref).max(), storage))
+        assert err <= tol, (name, shape, storage, n, err, tol)
+
+
+@pytest.mark.parametrize("orders", [(6, 2), (2, 2)], ids=["M4", "M5"])
+@pytest.mark.parametrize("name", ["field", "shan_chen"])
+def test_pair_kernel_hermite_orders_match_oracle(orc, name, orders):
+    """M4 / M5 through the two-nodes-per-thread kernel (FP16, 66 x 5 x 4) against the oracle's
+    literal collision, from a state with |u| ~ 0.1."""
+    nx, ny, nz = 66, 5, 4
+    eq, fo = orders
+    g = _moving_state(orc, nx, ny, nz, seed=41)
+    kw, okw = dict(nu=0.05), dict(nu=0.05, collision=orc.COLL_LITERAL)
+    if name == "field":
+        F = inputs.random_force_field(nx, ny, nz, seed=42, amp=5e-2)
+        force = ("field", None, F[0], F[1], F[2])
+        okw.update(force_kind=orc.FORCE_FIELD, field=F.astype(np.float64))
+    else:
+        kw.update(nu=0.1)
+        okw.update(nu=0.1, force_kind=orc.FORCE_SHAN_CHEN, G=-5.5)
+        force = ("shan_chen", (-5.5,))
+    s = Solver(nx, ny, nz, storage="fp16", **kw)
+    s.set_force(*force)
+    s.set_hermite_orders(eq, fo)
+    s.set_populations(g)
+    og = orc.Grid(nx, ny, nz, eq_order=eq, force_order=fo, **okw)
+    f = full(orc, storage_round(g, "fp16"))
+    S = scale(orc, f, og)
+    for n in (1, 2, 3):
+        s.step(1)
+        f = og.step(f, 1)
+        ref = dev(orc, f)
+        err = np.abs(s.get_populations().astype(np.float64) - ref).max()
+        tol = n * (C_STEP * EPS32 * S + half_ulp(np.abs(ref).max(), "fp16"))
+        assert err <= tol, (name, orders, n, err, tol)

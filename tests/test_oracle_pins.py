@@ -231,6 +231,43 @@ def test_single_rate_literal_collision_is_bgk(orc):
         assert np.abs(lit.collide(f, F) - bgk.collide(f, F)).max() < 5e-16 * 30
 
 
+def test_truncated_single_rate_literal_is_textbook_guo_bgk(orc):
+    """Models M4/M5 of Sec. III through the literal definition: with Lambda = omega I and both
+    expansions cut at H^(2), the CM collision is BGK with the classical second-order equilibrium
+    and Guo et al.'s forcing term, both written out here from their textbook forms."""
+    rng = np.random.default_rng(31)
+    c, w = orc.velocities().astype(float), orc.weights()
+    for _ in range(20):
+        om = rng.uniform(0.3, 1.95)
+        f, F = _rand_state(orc, rng, umax=0.2)
+        rho, u = _macro(c, f, F)
+        cu = c @ u
+        feq2 = w * rho * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * (u @ u))
+        guo = w * (3 * (c - u) @ F + 9 * cu * (c @ F))
+        lit = orc.Grid(1, 1, 1, omega=om, collision=orc.COLL_LITERAL, lambdas=[om] * 27, eq_order=2, force_order=2)
+        ex = f + om * (feq2 - f) + (1 - om / 2) * guo
+        assert np.abs(lit.collide(f, F) - ex).max() < 1e-14
+
+
+@pytest.mark.parametrize("orders", [(6, 2), (2, 2), (2, 6)])
+def test_truncations_change_only_moments_of_order_three_and_up(orc, orders):
+    """With the paper's Lambda, cutting f^eq and/or F_i at H^(2) leaves the post-collision central
+    moments k0..k9 (orders <= 2, including the omega-relaxed k4..k8) unchanged: the D3Q27
+    quadrature reproduces the second-order moments of every truncation of order >= 2."""
+    rng = np.random.default_rng(32)
+    c = orc.velocities().astype(float)
+    for _ in range(20):
+        om = rng.uniform(0.5, 1.99)
+        f, F = _rand_state(orc, rng, umax=0.2)
+        _, u = _macro(c, f, F)
+        full6 = orc.Grid(1, 1, 1, omega=om, collision=orc.COLL_LITERAL).collide(f, F)
+        trunc = orc.Grid(1, 1, 1, omega=om, collision=orc.COLL_LITERAL, eq_order=orders[0],
+                         force_order=orders[1]).collide(f, F)
+        dk = orc.central_moments(u, trunc - full6)
+        assert np.abs(dk[:10]).max() < 1e-15
+        assert np.abs(dk[10:]).max() > 1e-6
+
+
 def test_paper_lambda_at_omega_one_is_bgk(orc):
     """Eq. eq:relaxationMatrix at omega = 1 is the identity, so the scheme is BGK at nu = 1/6."""
     rng = np.random.default_rng(10)
