@@ -92,6 +92,17 @@ def lib():
         L.orc_step_sampled.argtypes = [ctypes.POINTER(_Desc), dp, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.c_int, dp]
         L.orc_step_sampled.restype = ctypes.c_int
+        L.orc_mhd_velocities.argtypes = [ctypes.POINTER(ctypes.c_int)]
+        L.orc_mhd_weights.argtypes = [dp]
+        L.orc_mhd_equilibrium.argtypes = [dp, dp, dp]
+        L.orc_mhd_moments.argtypes = [dp, dp, dp]
+        L.orc_mhd_node.argtypes = [dp, dp, dp, ctypes.c_double, dp, dp, dp, dp]
+        L.orc_mhd_init.argtypes = [ctypes.POINTER(_Desc), dp, dp, dp]
+        L.orc_mhd_init.restype = ctypes.c_int
+        L.orc_mhd_step.argtypes = [ctypes.POINTER(_Desc), ctypes.c_double, dp, dp, dp, ctypes.c_int]
+        L.orc_mhd_step.restype = ctypes.c_int
+        L.orc_mhd_fields.argtypes = [ctypes.POINTER(_Desc), ctypes.c_double, dp, dp, dp, dp, dp, dp]
+        L.orc_mhd_fields.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -251,6 +262,88 @@ class Grid:
         u = np.zeros((3,) + self.shape)
         self._check(lib().orc_macroscopic(ctypes.byref(self.desc), _dp(f), _dp(rho), _dp(u)), "macroscopic")
         return rho, u
+
+
+# --------------------------------------------------------------------------- magnetic field (App. C)
+QM = 7
+
+
+def mhd_velocities() -> np.ndarray:
+    c = (ctypes.c_int * (QM * 3))()
+    lib().orc_mhd_velocities(c)
+    return np.array(list(c), dtype=np.int64).reshape(QM, 3)
+
+
+def mhd_weights() -> np.ndarray:
+    w = np.zeros(QM)
+    lib().orc_mhd_weights(_dp(w))
+    return w
+
+
+def mhd_equilibrium(b, u) -> np.ndarray:
+    """h_la^eq as an array (7, 3)."""
+    out = np.zeros(3 * QM)
+    lib().orc_mhd_equilibrium(_dp(_vec(b)), _dp(_vec(u)), _dp(out))
+    return out.reshape(QM, 3)
+
+
+def mhd_moments(h):
+    """b = sum_l h_l and E_g = eps_gba sum_l xi_lb h_la of one node, h shaped (7, 3)."""
+    b, E = np.zeros(3), np.zeros(3)
+    lib().orc_mhd_moments(_dp(_vec(np.asarray(h).reshape(-1), 3 * QM)), _dp(b), _dp(E))
+    return b, E
+
+
+def mhd_node(f, h, Fext, omega_m):
+    """rho, u, Lorentz force, current of one node."""
+    rho = np.zeros(1)
+    u, FL, j = np.zeros(3), np.zeros(3), np.zeros(3)
+    lib().orc_mhd_node(_dp(_vec(f, Q)), _dp(_vec(np.asarray(h).reshape(-1), 3 * QM)), _dp(_vec(Fext)),
+                       float(omega_m), _dp(rho), _dp(u), _dp(FL), _dp(j))
+    return float(rho[0]), u, FL, j
+
+
+class MhdGrid(Grid):
+    """A Grid with the magnetic populations of App. C: h has shape (21, nz, ny, nx), entry 3 l + a."""
+
+    def __init__(self, nx, ny, nz, eta=None, omega_m=None, b_wall=(0.0, 0.0, 0.0), **kw):
+        super().__init__(nx, ny, nz, **kw)
+        if omega_m is None:
+            omega_m = 1.0 / (eta / 0.25 + 0.5)
+        self.omega_m = float(omega_m)
+        self.b_wall = _vec(b_wall)
+
+    def _field3(self, v):
+        """(3,) constant or (3, nz, ny, nx) field -> contiguous (3, N) float64."""
+        v = np.asarray(v, dtype=np.float64)
+        if v.ndim == 1:
+            v = v.reshape(3, 1, 1, 1)
+        return np.ascontiguousarray(np.broadcast_to(v, (3,) + self.shape)).reshape(3, -1)
+
+    def mhd_init(self, b, u) -> np.ndarray:
+        """h = h^eq(b, u)."""
+        b, u = self._field3(b), self._field3(u)
+        h = np.zeros((3 * QM,) + self.shape)
+        self._check(lib().orc_mhd_init(ctypes.byref(self.desc), _dp(b), _dp(u), _dp(h)), "mhd_init")
+        return h
+
+    def mhd_step(self, f, h, nsteps=1):
+        """Advance copies of f and h by nsteps of the coupled scheme; returns (f, h)."""
+        f = np.ascontiguousarray(f, dtype=np.float64).copy()
+        h = np.ascontiguousarray(h, dtype=np.float64).copy()
+        self._check(lib().orc_mhd_step(ctypes.byref(self.desc), self.omega_m, _dp(self.b_wall), _dp(f), _dp(h),
+                                       int(nsteps)), "mhd_step")
+        return f, h
+
+    def mhd_fields(self, f, h):
+        """rho, u, b, j at the current time."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        rho = np.zeros(self.shape)
+        u, b, j = (np.zeros((3,) + self.shape) for _ in range(3))
+        self._check(lib().orc_mhd_fields(ctypes.byref(self.desc), self.omega_m, _dp(f), _dp(h), _dp(rho), _dp(u),
+                                         _dp(b), _dp(j)), "mhd_fields")
+        return rho, u, b, j
 
 
 # --------------------------------------------------------------------------- diagnostics

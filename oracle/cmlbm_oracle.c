@@ -641,3 +641,187 @@ int orc_step_sampled(const orc_desc* d, const double* f, const long long* nodes,
     free(psi);
     return err;
 }
+
+/* ------------------------------------------------------------------ magnetic field (App. C) */
+static const int XI[ORC_QM][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+static const double CSM2 = 0.25; /* c_s^2 of D3Q7 (c_s = 1/2, App. C) */
+
+static double wm(int l) { return l == 0 ? 0.25 : 0.125; }
+static int opp_m(int l) { return l == 0 ? 0 : (l % 2 ? l + 1 : l - 1); }
+
+void orc_mhd_velocities(int xi[ORC_QM * 3]) {
+    for (int l = 0; l < ORC_QM; ++l)
+        for (int a = 0; a < 3; ++a) xi[3 * l + a] = XI[l][a];
+}
+
+void orc_mhd_weights(double w[ORC_QM]) {
+    for (int l = 0; l < ORC_QM; ++l) w[l] = wm(l);
+}
+
+/* App. C: h_la^eq = w_l [b_a + 4 xi_lb (u_b b_a - b_b u_a)] */
+void orc_mhd_equilibrium(const double b[3], const double u[3], double heq[ORC_QM * 3]) {
+    for (int l = 0; l < ORC_QM; ++l)
+        for (int a = 0; a < 3; ++a) {
+            double s = 0.0;
+            for (int c = 0; c < 3; ++c) s += XI[l][c] * (u[c] * b[a] - b[c] * u[a]);
+            heq[3 * l + a] = wm(l) * (b[a] + 4.0 * s);
+        }
+}
+
+void orc_mhd_moments(const double h[ORC_QM * 3], double b[3], double E[3]) {
+    double L[3][3] = {{0}}; /* electric tensor L[beta][alpha] = sum_l xi_lb h_la */
+    b[0] = b[1] = b[2] = 0.0;
+    for (int l = 0; l < ORC_QM; ++l)
+        for (int a = 0; a < 3; ++a) {
+            b[a] += h[3 * l + a];
+            for (int c = 0; c < 3; ++c) L[c][a] += XI[l][c] * h[3 * l + a];
+        }
+    /* E_g = eps_gba L[b][a] */
+    E[0] = L[1][2] - L[2][1];
+    E[1] = L[2][0] - L[0][2];
+    E[2] = L[0][1] - L[1][0];
+}
+
+static void cross(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+void orc_mhd_node(const double f[ORC_Q], const double h[ORC_QM * 3], const double Fext[3], double omega_m,
+                  double* rho, double u[3], double FL[3], double j[3]) {
+    double r = 0.0, m1[3] = {0, 0, 0}, b[3], E[3], Exb[3], s[3];
+    for (int i = 0; i < ORC_Q; ++i) {
+        r += f[i];
+        m1[0] += f[i] * CX[i];
+        m1[1] += f[i] * CY[i];
+        m1[2] += f[i] * CZ[i];
+    }
+    orc_mhd_moments(h, b, E);
+    const double kappa = omega_m / CSM2;
+    cross(E, b, Exb);
+    /* rho u = m1 + F_ext/2 + F_L/2 with F_L = -kappa E x b + 2 kappa ((u.b) b - |b|^2 u):
+       the component of u along b sees rho, the perpendicular part rho + kappa |b|^2 */
+    for (int a = 0; a < 3; ++a) s[a] = m1[a] + 0.5 * Fext[a] - 0.5 * kappa * Exb[a];
+    const double bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    if (bb > 0.0) {
+        const double sb = (s[0] * b[0] + s[1] * b[1] + s[2] * b[2]) / bb;
+        for (int a = 0; a < 3; ++a) {
+            const double par = sb * b[a];
+            u[a] = par / r + (s[a] - par) / (r + kappa * bb);
+        }
+    } else {
+        for (int a = 0; a < 3; ++a) u[a] = s[a] / r;
+    }
+    double uxb[3];
+    cross(u, b, uxb);
+    for (int a = 0; a < 3; ++a) j[a] = -kappa * (E[a] - 2.0 * uxb[a]);
+    cross(j, b, FL);
+    *rho = r;
+}
+
+static int check_mhd(const orc_desc* d) {
+    int st = check_desc(d);
+    if (st) return st;
+    if (d->mask || (d->force_kind != ORC_FORCE_NONE && d->force_kind != ORC_FORCE_UNIFORM)) return ORC_ERR_ARG;
+    return ORC_OK;
+}
+
+static void gather_h(const double* h, long long N, long long n, double out[ORC_QM * 3]) {
+    for (int k = 0; k < 3 * ORC_QM; ++k) out[k] = h[(long long)k * N + n];
+}
+
+int orc_mhd_init(const orc_desc* d, const double* b3, const double* u3, double* h) {
+    int st = check_mhd(d);
+    if (st) return st;
+    long long N = (long long)d->nx * d->ny * d->nz;
+#pragma omp parallel for schedule(static)
+    for (long long n = 0; n < N; ++n) {
+        double b[3] = {b3[n], b3[N + n], b3[2 * N + n]}, u[3] = {u3[n], u3[N + n], u3[2 * N + n]}, heq[3 * ORC_QM];
+        orc_mhd_equilibrium(b, u, heq);
+        for (int k = 0; k < 3 * ORC_QM; ++k) h[(long long)k * N + n] = heq[k];
+    }
+    return ORC_OK;
+}
+
+int orc_mhd_step(const orc_desc* d, double omega_m, const double b_wall[3], double* f, double* h, int nsteps) {
+    int st = check_mhd(d);
+    if (st) return st;
+    long long N = (long long)d->nx * d->ny * d->nz;
+    double* fs = (double*)malloc(sizeof(double) * Q * N);
+    double* hs = (double*)malloc(sizeof(double) * 3 * ORC_QM * N);
+    if (!fs || !hs) {
+        free(fs);
+        free(hs);
+        return ORC_ERR_NOMEM;
+    }
+    const double Fext[3] = {d->force_kind == ORC_FORCE_UNIFORM ? d->force[0] : 0.0,
+                            d->force_kind == ORC_FORCE_UNIFORM ? d->force[1] : 0.0,
+                            d->force_kind == ORC_FORCE_UNIFORM ? d->force[2] : 0.0};
+    int err = ORC_OK;
+    for (int s = 0; s < nsteps && !err; ++s) {
+        /* collision of both populations */
+#pragma omp parallel for schedule(static) reduction(| : err)
+        for (long long n = 0; n < N; ++n) {
+            double fl[Q], fo[Q], hl[3 * ORC_QM], heq[3 * ORC_QM], rho, u[3], FL[3], j[3], F[3], b[3], E[3];
+            gather_node(f, N, n, fl);
+            gather_h(h, N, n, hl);
+            orc_mhd_node(fl, hl, Fext, omega_m, &rho, u, FL, j);
+            for (int a = 0; a < 3; ++a) F[a] = Fext[a] + FL[a];
+            err |= orc_collide(d, fl, F, fo);
+            for (int i = 0; i < Q; ++i) fs[(long long)i * N + n] = fo[i];
+            orc_mhd_moments(hl, b, E);
+            orc_mhd_equilibrium(b, u, heq);
+            for (int k = 0; k < 3 * ORC_QM; ++k) hs[(long long)k * N + n] = hl[k] + omega_m * (heq[k] - hl[k]);
+        }
+        /* streaming: pull from x - c; fluid halfway bounce-back, magnetic anti-bounce-back at walls */
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < d->nz; ++z)
+            for (int y = 0; y < d->ny; ++y)
+                for (int x = 0; x < d->nx; ++x) {
+                    long long n = node_index(d, x, y, z);
+                    for (int i = 0; i < Q; ++i) {
+                        long long src = neighbour(d, x, y, z, i, -1);
+                        f[(long long)i * N + n] = (src >= 0) ? fs[(long long)i * N + src]
+                                                             : fs[(long long)orc_opposite(i) * N + n];
+                    }
+                    for (int l = 0; l < ORC_QM; ++l) {
+                        /* D3Q7 velocity l is D3Q27 velocity l (the first seven of Sec. II) */
+                        long long src = neighbour(d, x, y, z, l, -1);
+                        for (int a = 0; a < 3; ++a) {
+                            h[(long long)(3 * l + a) * N + n] =
+                                (src >= 0) ? hs[(long long)(3 * l + a) * N + src]
+                                           : -hs[(long long)(3 * opp_m(l) + a) * N + n] + 2.0 * wm(l) * b_wall[a];
+                        }
+                    }
+                }
+    }
+    free(fs);
+    free(hs);
+    return err;
+}
+
+int orc_mhd_fields(const orc_desc* d, double omega_m, const double* f, const double* h, double* rho, double* u3,
+                   double* b3, double* j3) {
+    int st = check_mhd(d);
+    if (st) return st;
+    long long N = (long long)d->nx * d->ny * d->nz;
+    const double Fext[3] = {d->force_kind == ORC_FORCE_UNIFORM ? d->force[0] : 0.0,
+                            d->force_kind == ORC_FORCE_UNIFORM ? d->force[1] : 0.0,
+                            d->force_kind == ORC_FORCE_UNIFORM ? d->force[2] : 0.0};
+#pragma omp parallel for schedule(static)
+    for (long long n = 0; n < N; ++n) {
+        double fl[Q], hl[3 * ORC_QM], r, u[3], FL[3], j[3], b[3], E[3];
+        gather_node(f, N, n, fl);
+        gather_h(h, N, n, hl);
+        orc_mhd_node(fl, hl, Fext, omega_m, &r, u, FL, j);
+        orc_mhd_moments(hl, b, E);
+        rho[n] = r;
+        for (int a = 0; a < 3; ++a) {
+            u3[a * N + n] = u[a];
+            b3[a * N + n] = b[a];
+            j3[a * N + n] = j[a];
+        }
+    }
+    return ORC_OK;
+}

@@ -100,6 +100,39 @@ int orc_step(const orc_desc* d, double* f, int nsteps);
 /* One step evaluated only at the listed nodes: out[k*27 + i] = f_i(nodes[k], t+1). */
 int orc_step_sampled(const orc_desc* d, const double* f, const long long* nodes, int count, double* out);
 
+/* ------------------------------------------------------------------ magnetic field (App. C)
+ * A second LBM on D3Q7 for the magnetic field b: vector populations h_l (l = 0..6, velocities
+ * xi_l = 0, +-x, +-y, +-z), stored h[(3*l + a)*N + n] (component a = x, y, z of population l),
+ * BGK with omega_m, eta = cs_m^2 (1/omega_m - 1/2), cs_m^2 = 1/4, weights 1/4 and 1/8,
+ *   h_la^eq = w_l [ b_a + 4 xi_lb (u_b b_a - b_b u_a) ],    b = sum_l h_l.
+ * Coupling (readings): the Lorentz force F_L = j x b is added to the fluid's force density; the
+ * current j = curl b comes from the non-equilibrium electric tensor of the pre-collision h,
+ * d_b b_a = -(omega_m / cs_m^2) sum_l xi_lb (h_la - h_la^eq), i.e. j = -(omega_m / cs_m^2)(E - 2 u x b)
+ * with E_g = eps_gba sum_l xi_lb h_la; u (which both h^eq and Eq. macroscopic use) and F_L are
+ * solved together, rho u = sum_i f_i c_i + (F_ext + F_L)/2, which is linear in u.  Walls: halfway
+ * (y = -1/2, ny - 1/2) anti-bounce-back h_l(x, t+1) = -h*_opp(l)(x, t) + 2 w_l b_wall, which holds
+ * b = b_wall on the wall to second order. */
+#define ORC_QM 7
+void orc_mhd_velocities(int xi[ORC_QM * 3]);
+void orc_mhd_weights(double w[ORC_QM]);
+/* h_la^eq, heq[3*l + a] */
+void orc_mhd_equilibrium(const double b[3], const double u[3], double heq[ORC_QM * 3]);
+/* b = sum_l h_l and E_g = eps_gba sum_l xi_lb h_la of one node's populations h[3*l + a] */
+void orc_mhd_moments(const double h[ORC_QM * 3], double b[3], double E[3]);
+/* rho, u, Lorentz force and current of one node from its fluid populations (27, full f), its
+ * magnetic populations and the external force density */
+void orc_mhd_node(const double f[ORC_Q], const double h[ORC_QM * 3], const double Fext[3], double omega_m,
+                  double* rho, double u[3], double FL[3], double j[3]);
+/* h = h^eq(b, u) on every node; b3, u3: 3N arrays (x block, y, z) */
+int orc_mhd_init(const orc_desc* d, const double* b3, const double* u3, double* h);
+/* nsteps of the coupled scheme: fluid collision (d->collision, force = F_ext + F_L; F_ext from
+ * d->force_kind NONE or UNIFORM), magnetic BGK, two-array streaming of both (fluid: halfway
+ * bounce-back; magnetic: anti-bounce-back with b_wall).  No masks. */
+int orc_mhd_step(const orc_desc* d, double omega_m, const double b_wall[3], double* f, double* h, int nsteps);
+/* rho (N), u, b, j (3N each) at the current time */
+int orc_mhd_fields(const orc_desc* d, double omega_m, const double* f, const double* h, double* rho, double* u3,
+                   double* b3, double* j3);
+
 #ifdef __cplusplus
 }
 #endif
