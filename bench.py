@@ -41,7 +41,12 @@ WORKLOADS = {
                            "of solid fraction U[0,0.2], nu~U[0.01,0.1], F_x~U[1e-6,1e-5]) in one batch"),
     "kolmogorov256": dict(n=256, kind="kolmogorov", nu=0.05, F0=1e-5,
                           text="Kolmogorov flow 256^3 periodic, nu=0.05, F_x=1e-5 sin(2 pi y/256)"),
+    "orszag_tang128": dict(n=128, kind="mhd", nu=0.005, eta=0.005, u0=0.0203, b0=0.0203,
+                           text="3D Orszag-Tang vortex 128^3 periodic (magnetic field on D3Q7, Lorentz force "
+                                "j x b), u0=b0=0.0203, nu=eta=0.005"),
 }
+# bytes per node of one step, AA in place: 27 populations read + written (+ 21 magnetic ones)
+MHD_BYTES_PER_NODE = 216 + 168
 
 
 def parse():
@@ -54,6 +59,8 @@ def parse():
     ap.add_argument("--storage", choices=["fp32", "fp16", "bf16"], default="fp32")
     ap.add_argument("--n", type=int, default=None, help="override the cube edge (profiling of smaller cases)")
     ap.add_argument("--count", type=int, default=None, help="override the number of batched domains")
+    ap.add_argument("--shape", default=None,
+                    help="batched launch shape tile,blocks_per_sm,schedule (e.g. 128,16,strided) instead of autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--budget-s", type=float, default=60.0,
                     help="reference arm: wall-time budget of warm-up plus timed oracle steps")
@@ -79,6 +86,9 @@ def initial_fields(wl):
         return rho, z, z, z
     if wl["kind"] == "tgv":
         return inputs.taylor_green(n, wl["u0"])
+    if wl["kind"] == "mhd":
+        u, _ = inputs.orszag_tang(n, wl["u0"], wl["b0"])
+        return np.ones((n, n, n), dtype=np.float32), u[0], u[1], u[2]
     one = np.ones((n, n, n), dtype=np.float32)
     z = np.zeros_like(one)
     return one, z, z, z
@@ -89,6 +99,43 @@ def configure_force(s, wl):
         s.set_force("shan_chen", (wl["G"],))
     elif wl["kind"] == "kolmogorov":
         s.set_force("kolmogorov", (wl["F0"],))
+
+
+def initial_magnetic(wl):
+    from paper_1905_10182_gb300 import inputs
+    return inputs.orszag_tang(wl["n"], wl["u0"], wl["b0"])[1]
+
+
+def oracle_grid(wl, m, threads):
+    """Oracle grid, initial state and step function for an m^3 sample of the workload."""
+    import numpy as np
+
+    import oracle
+    sub = dict(wl, n=m)
+    if wl["kind"] == "droplet":
+        sub["radius"] = max(3.0, wl["radius"] * m / wl["n"])
+    rho, ux, uy, uz = initial_fields(sub)
+    u = np.stack([ux, uy, uz]).astype(np.float64)
+    kw = dict(nu=wl["nu"], collision=oracle.COLL_PAPER, threads=threads)
+    if wl["kind"] == "droplet":
+        kw.update(force_kind=oracle.FORCE_SHAN_CHEN, G=wl["G"])
+    elif wl["kind"] == "kolmogorov":
+        kw.update(force_kind=oracle.FORCE_KOLMOGOROV, force=(wl["F0"], 0, 0))
+    if wl["kind"] == "mhd":
+        g = oracle.MhdGrid(m, m, m, eta=wl["eta"], **kw)
+        f = g.init_equilibrium(rho.astype(np.float64), u)
+        h = g.mhd_init(initial_magnetic(sub).astype(np.float64), u)
+        state = [f, h]
+
+        def step(k):
+            state[0], state[1] = g.mhd_step(state[0], state[1], k)
+        return step
+    g = oracle.Grid(m, m, m, **kw)
+    state = [g.init_equilibrium(rho.astype(np.float64), u)]
+
+    def step(k):
+        state[0] = g.step(state[0], k)
+    return step
 
 
 # --------------------------------------------------------------------------- clocks
@@ -152,25 +199,15 @@ def oracle_mlups(wl, target_s=12.0, threads=None):
     import oracle
     threads = threads or os.cpu_count() or 1
     n = wl["n"]
-    rho, ux, uy, uz = initial_fields(wl)
-    kw = dict(nu=wl["nu"], collision=oracle.COLL_PAPER, threads=threads)
-    if wl["kind"] == "droplet":
-        kw.update(force_kind=oracle.FORCE_SHAN_CHEN, G=wl["G"])
-    elif wl["kind"] == "kolmogorov":
-        kw.update(force_kind=oracle.FORCE_KOLMOGOROV, force=(wl["F0"], 0, 0))
-    sample_n = n
-    # a 512^3 FP64 oracle state (29 GB x 2) does not fit a bounded sample: use a 128^3 corner box
-    if n > 128:
-        sample_n = 128
-        rho, ux, uy, uz = (a[:sample_n, :sample_n, :sample_n] for a in (rho, ux, uy, uz))
-    g = oracle.Grid(sample_n, sample_n, sample_n, **kw)
-    f = g.init_equilibrium(rho.astype(np.float64), np.stack([ux, uy, uz]).astype(np.float64))
+    # a 512^3 FP64 oracle state (29 GB x 2) does not fit a bounded sample: use a 128^3 box
+    sample_n = min(n, 128)
+    step = oracle_grid(wl, sample_n, threads)
     t0 = time.perf_counter()
-    f = g.step(f, 1)
+    step(1)
     t1 = time.perf_counter() - t0
     steps = max(1, min(200, int(target_s / max(t1, 1e-6))))
     t0 = time.perf_counter()
-    g.step(f, steps)
+    step(steps)
     dt = time.perf_counter() - t0
     nodes = sample_n ** 3
     return {"value": nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
@@ -194,21 +231,10 @@ def run_reference(args, wl):
     per_node = 1.0 / (probe["value"] * 1e6)
     budget = args.budget_s / max(1, args.steps + args.warmup)
     m = int(max(8, min(wl["n"], (budget / per_node) ** (1.0 / 3.0))))
-    sub = dict(wl, n=m)
-    if wl["kind"] == "droplet":
-        sub["radius"] = max(3.0, wl["radius"] * m / wl["n"])
-    import numpy as np
-    rho, ux, uy, uz = initial_fields(sub)
-    kw = dict(nu=wl["nu"], collision=oracle.COLL_PAPER, threads=threads)
-    if wl["kind"] == "droplet":
-        kw.update(force_kind=oracle.FORCE_SHAN_CHEN, G=wl["G"])
-    elif wl["kind"] == "kolmogorov":
-        kw.update(force_kind=oracle.FORCE_KOLMOGOROV, force=(wl["F0"], 0, 0))
-    g = oracle.Grid(m, m, m, **kw)
-    f = g.init_equilibrium(rho.astype(np.float64), np.stack([ux, uy, uz]).astype(np.float64))
-    f = g.step(f, args.warmup)
+    step = oracle_grid(wl, m, threads)
+    step(args.warmup)
     t0 = time.perf_counter()
-    g.step(f, args.steps)
+    step(args.steps)
     dt = time.perf_counter() - t0
     val = m ** 3 * args.steps / dt / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
@@ -229,7 +255,7 @@ def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1905_10182_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name in ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_x2.cuh", "lbm_launch.h") or \
+        if name in ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_x2.cuh") or \
                 (name.startswith("lbm_k_") and name.endswith(".cu")):
             h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
@@ -274,7 +300,12 @@ def run_batch(args, wl):
     fluid = int(sum(int((d["mask"] == 0).sum()) for d in doms))
     nodes = int(sum(d["nx"] * d["ny"] * d["nz"] for d in doms))
     b = BatchSolver(doms)
-    tune = b.autotune(trial_steps=10)
+    if args.shape:
+        tile, bps, sch = args.shape.split(",")
+        b.set_shape(int(tile), int(bps), sch)
+        tune = {"fixed": args.shape}
+    else:
+        tune = b.autotune(trial_steps=10)
     b.step(args.warmup)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -363,6 +394,10 @@ def run_ours(args, wl):
     configure_force(s, wl)
     s.set_state(torch.from_numpy(rho).cuda(), torch.from_numpy(ux).cuda(), torch.from_numpy(uy).cuda(),
                 torch.from_numpy(uz).cuda())
+    mhd = wl["kind"] == "mhd"
+    if mhd:
+        bmag = initial_magnetic(wl)
+        s.set_magnetic(wl["eta"], b=[torch.from_numpy(a).cuda() for a in bmag])
     s.step(args.warmup)
     s.synchronize()
     stream = torch.cuda.current_stream()
@@ -394,6 +429,7 @@ def run_ours(args, wl):
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     pin = [torch.from_numpy(a).pin_memory() for a in (rho, ux, uy, uz)]
+    pin_b = [torch.from_numpy(a).pin_memory() for a in bmag] if mhd else None
     out = [torch.empty(a.shape, dtype=torch.float32).pin_memory() for a in (rho, ux, uy, uz)]
     e = Solver(n, n, n, nu=wl["nu"], storage=args.storage)
     configure_force(e, wl)
@@ -401,6 +437,8 @@ def run_ours(args, wl):
     barrier()
     t0 = time.perf_counter()
     e.set_state(*pin)
+    if mhd:
+        e.set_magnetic(wl["eta"], b=pin_b)
     e.step(args.steps)
     e.macroscopic(*out)
     torch.cuda.synchronize()
@@ -412,9 +450,11 @@ def run_ours(args, wl):
         t_e2e = float(t.item())
     e.close()
     e2e = {"value": world * nodes * args.steps / t_e2e / 1e6, "unit": "MLUPS",
-           "h2d_bytes_per_step": 16 * nodes / args.steps, "d2h_bytes_per_step": 16 * nodes / args.steps,
-           "note": "set_state from pinned host rho,u (16 B/node) + K steps + macroscopic to pinned host "
-                   "(16 B/node); bytes per step are the job's totals / K"}
+           "h2d_bytes_per_step": (28 if mhd else 16) * nodes / args.steps,
+           "d2h_bytes_per_step": 16 * nodes / args.steps,
+           "note": "set_state from pinned host rho,u (16 B/node)" + (" and set_magnetic from pinned host b (12 B/node)"
+                                                                     if mhd else "") +
+                   " + K steps + macroscopic to pinned host (16 B/node); bytes per step are the job's totals / K"}
 
     if rank != 0:
         if world > 1:
@@ -426,7 +466,7 @@ def run_ours(args, wl):
     peak = peaks.get("hbm_gbs")
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
-    bpn = BYTES_PER_NODE[args.storage]
+    bpn = MHD_BYTES_PER_NODE if mhd else BYTES_PER_NODE[args.storage]
     coll_avg_ms = prof["collide_ms"] / max(1, prof["collide_launches"])
     achieved = bpn * nodes / (coll_avg_ms * 1e-3) / 1e9
     traffic = committed_traffic(args.workload, args.storage)
@@ -450,7 +490,7 @@ def run_ours(args, wl):
                    "l2": f"inputs larger than L2: population store {27 * nodes * (4 if args.storage == 'fp32' else 2) / 1e6:.0f} MB"
                          " > 129 MB, swept in full every step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "k_stream_collide",
+                     "traffic": traffic, "kernel": "k_mhd_step" if mhd else "k_stream_collide",
                      "algorithmic_bytes_per_launch": bpn * nodes, "avg_launch_ms": coll_avg_ms,
                      "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback 6.8 TB/s"},
         "kernel_ms_per_step": {"stream_collide": coll_avg_ms,

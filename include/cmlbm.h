@@ -119,6 +119,29 @@ LBM_API lbm_status lbm_set_force(lbm_ctx* ctx, int kind, const double* params, c
  * u = 0).  Orders other than 2 and 6: LBM_ERR_UNSUPPORTED. */
 LBM_API lbm_status lbm_set_hermite_orders(lbm_ctx* ctx, int eq_order, int force_order);
 
+/* Magnetic field (App. C): turns on a second LBM for the magnetic field b on D3Q7 (vector
+ * populations h_l, l = rest, +-x, +-y, +-z; BGK with omega_m, eta = (1/omega_m - 1/2) / 4;
+ * h_la^eq = w_l [b_a + 4 xi_lb (u_b b_a - b_b u_a)], w = 1/4, 1/8; b = sum_l h_l), coupled to the
+ * fluid through the Lorentz force j x b added to the force density (Sec. III, Hartmann flow and
+ * Orszag-Tang vortex).  The current is read from the populations: j = -(4 omega_m)(E - 2 u x b),
+ * E_g = eps_gba sum_l xi_lb h_la (pre-collision), with u and j solved together from
+ * rho u = sum f c + (F + j x b)/2 (linear in u).  At y walls the field b_wall (3 doubles, NULL:
+ * zero) is held by anti-bounce-back.  Initial state h = h^eq(b, u) with u of the current fluid
+ * state; bx, by, bz: N floats each (host or device; NULL: zero).  Every later lbm_step advances
+ * both; lbm_macroscopic and lbm_stats include j x b / 2 in u.  Needs FP32 storage, no solid mask,
+ * no z slab, force NONE or UNIFORM, even parity (after lbm_set_state or an even number of
+ * steps): else LBM_ERR_UNSUPPORTED / LBM_ERR_STATE.  eta > 0.  Adds 84 B per node. */
+LBM_API lbm_status lbm_set_magnetic(lbm_ctx* ctx, double eta, const double b_wall[3], const float* bx,
+                                    const float* by, const float* bz);
+
+/* Magnetic populations at the current time, natural order h[(3 l + a) N + n] (21 N floats, host
+ * or device).  Set: only at even parity; get: any time.  LBM_ERR_STATE without a magnetic field. */
+LBM_API lbm_status lbm_get_magnetic_populations(lbm_ctx* ctx, float* h);
+LBM_API lbm_status lbm_set_magnetic_populations(lbm_ctx* ctx, const float* h);
+
+/* b and j = curl b at the current time (N floats each, host or device, NULL to skip); syncs. */
+LBM_API lbm_status lbm_magnetic(lbm_ctx* ctx, float* bx, float* by, float* bz, float* jx, float* jy, float* jz);
+
 /* Sets f = f^eq(rho, u), the complete (sixth-order Hermite) equilibrium of Eq. eq:truncation,
  * on every fluid node (rest state on solid nodes).  Arrays: N floats each, host or device.
  * Resets the step counter to 0. */
@@ -165,7 +188,8 @@ LBM_API lbm_status lbm_halo_unpack(lbm_ctx* ctx, int face, int stage, const void
  * step counter, AA parity) and the raw population store to path; lbm_load reads it back into a
  * context created with the same grid, storage and boundaries (LBM_ERR_STATE otherwise) and
  * restores the step counter and parity, so that a resumed run continues bit for bit.  Force
- * fields and masks are not saved: set them again on the new context.  Both wait for the stream. */
+ * fields and masks are not saved: set them again on the new context.  Both wait for the stream.
+ * A context with a magnetic field (lbm_set_magnetic): LBM_ERR_UNSUPPORTED. */
 LBM_API lbm_status lbm_save(lbm_ctx* ctx, const char* path);
 LBM_API lbm_status lbm_load(lbm_ctx* ctx, const char* path);
 
@@ -233,11 +257,19 @@ typedef struct {
 LBM_API lbm_status lbm_batch_create(const lbm_domain* domains, int count, double rho0, void* stream, lbm_batch** out);
 
 /* Times trial_steps (rounded to even, >= 2) graph-replayed steps for each candidate launch shape
- * (64, 128, 256 nodes per tile; 1/2x, 1x, 4x the resident blocks per SM, or one block per tile)
- * and keeps the fastest.  out (optional, 3 doubles): best MLUPS, nodes per tile, blocks per SM
- * (0: one block per tile).  The trials advance the
- * state, so afterwards every domain is reset to rest: call it before lbm_batch_set_state. */
+ * and keeps the fastest.  Candidates: 64, 128, 256 nodes per tile; schedule 0, strided (block b
+ * takes tiles b, b + grid, ...), at 1/2x, 1x, 4x the resident blocks per SM or one block per tile;
+ * schedule 1, contiguous (each block one run of consecutive tiles) and schedule 2, strided, both
+ * prefetching the block's next tile into L2, at 1/2x, 1x, 4x.  out (optional, 4 doubles): best
+ * MLUPS, nodes per tile, blocks per SM (0: one block per tile), schedule.  The trials advance
+ * the state, so afterwards every domain is reset to rest: call it before lbm_batch_set_state. */
 LBM_API lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, double* out);
+
+/* Sets the launch shape directly (a shape lbm_batch_autotune reported, for instance):
+ * nodes_per_tile in {64, 128, 256}, 0 <= blocks_per_sm <= 64 (0: one block per tile), schedule 0
+ * (strided), 1 (contiguous, prefetching) or 2 (strided, prefetching).  The state is not touched;
+ * results do not depend on the shape. */
+LBM_API lbm_status lbm_batch_set_shape(lbm_batch* b, int nodes_per_tile, int blocks_per_sm, int schedule);
 
 /* Enqueues nsteps steps of every active domain. */
 LBM_API lbm_status lbm_batch_step(lbm_batch* b, int nsteps);

@@ -74,6 +74,14 @@ def lib():
         L.lbm_set_force.restype = st
         L.lbm_set_hermite_orders.argtypes = [_P, ctypes.c_int, ctypes.c_int]
         L.lbm_set_hermite_orders.restype = st
+        L.lbm_set_magnetic.argtypes = [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _P, _P, _P]
+        L.lbm_set_magnetic.restype = st
+        L.lbm_get_magnetic_populations.argtypes = [_P, _P]
+        L.lbm_get_magnetic_populations.restype = st
+        L.lbm_set_magnetic_populations.argtypes = [_P, _P]
+        L.lbm_set_magnetic_populations.restype = st
+        L.lbm_magnetic.argtypes = [_P] + [_P] * 6
+        L.lbm_magnetic.restype = st
         L.lbm_set_state.argtypes = [_P, _P, _P, _P, _P]
         L.lbm_set_state.restype = st
         L.lbm_set_populations.argtypes = [_P, _P]
@@ -101,6 +109,8 @@ def lib():
         L.lbm_batch_create.restype = st
         L.lbm_batch_autotune.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         L.lbm_batch_autotune.restype = st
+        L.lbm_batch_set_shape.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.lbm_batch_set_shape.restype = st
         L.lbm_batch_step.argtypes = [_P, ctypes.c_int]
         L.lbm_batch_step.restype = st
         L.lbm_batch_run.argtypes = [_P, ctypes.c_double, ctypes.c_longlong, ctypes.c_int,

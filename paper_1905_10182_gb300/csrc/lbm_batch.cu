@@ -69,25 +69,52 @@ __device__ __forceinline__ void decode(uint32_t n, const BatchDomain& d, int& x,
     y = (int)(r - zz * d.ny);
 }
 
-// One AA step of every node of every active tile (persistent: blocks stride over the tile list).
-template <bool ODD>
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// One AA step of every node of every active tile.  Blocks are persistent.  Schedules:
+//  0 strided: block b takes tiles b, b + grid, b + 2 grid, ...; the tiles in flight form one
+//    compact wavefront through the tile list, so an odd step finds the rows and planes its
+//    neighbours share in L2;
+//  1 contiguous: block b takes one contiguous run of the tile list, prefetching the next tile;
+//  2 strided with prefetch: the strided order, and while a tile is computed the link words and the
+//    27 population lines of the block's next tile are prefetched into L2 (no registers held).
+// The prefetch is issued after the tile's own gathers, so that its descriptor loads overlap their
+// latency.
+template <bool ODD, int SCHED>
 __global__ void __launch_bounds__(256, 2) k_batch_step(const BatchDomain* __restrict__ dom, const BatchTile* __restrict__ tiles,
                                                     const int* __restrict__ ntiles_p, float* __restrict__ pool,
                                                     const uint32_t* __restrict__ links, unsigned int* flag, float rho0) {
     const int ntiles = *ntiles_p;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int t = blockIdx.x, t_end = ntiles, t_step = gridDim.x;
+    if (SCHED == 1) {
+        t = (int)((long long)ntiles * blockIdx.x / gridDim.x);
+        t_end = (int)((long long)ntiles * (blockIdx.x + 1) / gridDim.x);
+        t_step = 1;
+    }
+    for (; t < t_end; t += t_step) {
         const BatchTile tl = tiles[t];
         const BatchDomain d = dom[tl.domain];
         const uint32_t n = tl.start + threadIdx.x;
+        float* f = pool + d.f_off;
         if (n >= d.N) continue;
         const uint32_t link = links[d.node_off + n];
         if (link & SOLID_BIT) continue;
         int x, y, z;
         decode(n, d, x, y, z);
         const Nbr nb = make_nbr(x, y, z, d);
-        float* f = pool + d.f_off;
         float g[27];
         aa_gather<float, ODD, true>(f, (long long)d.N, nb, link, g);
+        if (SCHED != 0 && t + t_step < t_end) {
+            const BatchTile nt = tiles[t + t_step];
+            const uint32_t nn = nt.start + threadIdx.x;
+            const uint32_t nN = dom[nt.domain].N;
+            if (nn < nN) {
+                const float* nf = pool + dom[nt.domain].f_off;
+                prefetch_l2(links + dom[nt.domain].node_off + nn);
+#pragma unroll
+                for (int i = 0; i < 27; ++i) prefetch_l2(nf + (long long)i * nN + nn);
+            }
+        }
         const Macro m = collide_cm(g, d.Fx, d.Fy, d.Fz, d.omega, rho0);
         const float u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
         const bool bad = !(m.rho > 0.0f) || !(u2 < 1.0f);
@@ -228,6 +255,7 @@ struct lbm_batch {
     // launch shape (autotuned)
     int threads = 128;
     int blocks_per_sm = 4;
+    int schedule = 0;  // 0 strided, 1 contiguous runs with prefetch, 2 strided with prefetch
     int sms = 0;
     int grid = 0;
 
@@ -291,20 +319,27 @@ lbm_status rebuild_tiles(lbm_batch* b) {
 }
 
 cudaError_t launch_batch_step(lbm_batch* b, int odd) {
-    if (odd)
-        k_batch_step<true><<<b->grid, b->threads, 0, b->stream>>>(b->d_dom, b->d_tiles, b->d_ntiles, b->pool, b->links,
-                                                                  b->d_flag, (float)b->rho0);
-    else
-        k_batch_step<false><<<b->grid, b->threads, 0, b->stream>>>(b->d_dom, b->d_tiles, b->d_ntiles, b->pool, b->links,
-                                                                   b->d_flag, (float)b->rho0);
+#define CMLBM_BATCH_LAUNCH(O, C)                                                                                  \
+    k_batch_step<O, C><<<b->grid, b->threads, 0, b->stream>>>(b->d_dom, b->d_tiles, b->d_ntiles, b->pool, b->links, \
+                                                               b->d_flag, (float)b->rho0)
+    switch (b->schedule * 2 + (odd ? 1 : 0)) {
+    case 0: CMLBM_BATCH_LAUNCH(false, 0); break;
+    case 1: CMLBM_BATCH_LAUNCH(true, 0); break;
+    case 2: CMLBM_BATCH_LAUNCH(false, 1); break;
+    case 3: CMLBM_BATCH_LAUNCH(true, 1); break;
+    case 4: CMLBM_BATCH_LAUNCH(false, 2); break;
+    default: CMLBM_BATCH_LAUNCH(true, 2); break;
+    }
+#undef CMLBM_BATCH_LAUNCH
     return cudaGetLastError();
 }
 
 // blocks_per_sm = 0: one block per tile (the grid covers the tile list at this time; later
 // retirements only shorten the list, so the grid stays large enough).
-lbm_status set_shape(lbm_batch* b, int threads, int blocks_per_sm) {
+lbm_status set_shape(lbm_batch* b, int threads, int blocks_per_sm, int schedule) {
     b->threads = threads;
     b->blocks_per_sm = blocks_per_sm;
+    b->schedule = schedule;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -500,16 +535,19 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, double* out) {
     trial_steps &= ~1;
     const int threads_c[3] = {64, 128, 256};
     double best = -1.0;
-    int best_t = b->threads, best_b = b->blocks_per_sm;
+    int best_t = b->threads, best_b = b->blocks_per_sm, best_c = b->schedule;
     for (int ti = 0; ti < 3; ++ti) {
         int occ = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_step<true>, threads_c[ti], 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_step<true, 0>, threads_c[ti], 0);
         if (e != cudaSuccess) return bcuda(b, e, "occupancy query");
         if (occ < 1) continue;
-        // persistent, half, oversubscribed, one block per tile
-        const int cand_b[4] = {occ, std::max(1, occ / 2), occ * 4, 0};
-        for (int bi = 0; bi < 4; ++bi) {
-            lbm_status st = set_shape(b, threads_c[ti], cand_b[bi]);
+        // strided: persistent, half, oversubscribed, one block per tile; contiguous with prefetch
+        // and strided with prefetch: persistent, half, oversubscribed
+        const int cand_b[10] = {occ, std::max(1, occ / 2), occ * 4, 0, occ, std::max(1, occ / 2), occ * 4,
+                                occ, std::max(1, occ / 2), occ * 4};
+        const int cand_c[10] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 2};
+        for (int bi = 0; bi < 10; ++bi) {
+            lbm_status st = set_shape(b, threads_c[ti], cand_b[bi], cand_c[bi]);
             if (st) return st;
             st = ensure_graph(b, trial_steps);
             if (st) return st;
@@ -537,10 +575,11 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, double* out) {
                 best = mlups;
                 best_t = threads_c[ti];
                 best_b = cand_b[bi];
+                best_c = cand_c[bi];
             }
         }
     }
-    lbm_status st = set_shape(b, best_t, best_b);
+    lbm_status st = set_shape(b, best_t, best_b, best_c);
     if (st) return st;
     // trial steps changed the state: return every domain to the rest state
     long long pop = 0;
@@ -555,8 +594,17 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, double* out) {
         out[0] = best;
         out[1] = best_t;
         out[2] = best_b;
+        out[3] = best_c;
     }
     return LBM_OK;
+}
+
+lbm_status lbm_batch_set_shape(lbm_batch* b, int nodes_per_tile, int blocks_per_sm, int schedule) {
+    if (!b) return LBM_ERR_ARG;
+    if ((nodes_per_tile != 64 && nodes_per_tile != 128 && nodes_per_tile != 256) || blocks_per_sm < 0 ||
+        blocks_per_sm > 64 || schedule < 0 || schedule > 2)
+        return bfail(b, LBM_ERR_ARG, "nodes_per_tile in {64, 128, 256}, 0 <= blocks_per_sm <= 64, schedule 0, 1 or 2");
+    return set_shape(b, nodes_per_tile, blocks_per_sm, schedule);
 }
 
 lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {

@@ -31,6 +31,7 @@ struct lbm_ctx {
     void* f = nullptr;  // population store
     bool own_f = false;
     uint32_t* links = nullptr;  // per-node link word (null: periodic, no mask, no walls)
+    bool has_mask = false;
 
     int force_kind = LBM_FORCE_NONE;
     float F[3] = {0, 0, 0};
@@ -40,7 +41,13 @@ struct lbm_ctx {
     float* field = nullptr; // 3N
     float* psi = nullptr;   // N
 
-    float* macro = nullptr;  // 4N: rho, ux, uy, uz
+    // magnetic field (App. C), off unless lbm_set_magnetic was called
+    float* hm = nullptr;     // 21 N: D3Q7 vector populations
+    double eta = 0;
+    float omega_m = 1;
+    float bw[3] = {0, 0, 0};  // b at the y walls
+
+    float* macro = nullptr;  // 4N: rho, ux, uy, uz (10N with the magnetic field: + b, j)
     float* uprev = nullptr;  // 3N
     bool have_uprev = false;
     double* partials = nullptr;
@@ -197,7 +204,7 @@ lbm_status sync_and_check(lbm_ctx* c) {
 }
 
 lbm_status ensure_macro(lbm_ctx* c) {
-    if (!c->macro) CK(c, cudaMalloc(&c->macro, sizeof(float) * 4 * c->NL), "cudaMalloc(macroscopic)");
+    if (!c->macro) CK(c, cudaMalloc(&c->macro, sizeof(float) * (c->hm ? 10 : 4) * c->NL), "cudaMalloc(macroscopic)");
     return LBM_OK;
 }
 
@@ -216,6 +223,10 @@ lbm_status run_macro(lbm_ctx* c) {
     if (st) return st;
     float* m = c->macro;
     const long long NL = c->NL;
+    if (c->hm) {
+        CK(c, launch_mhd_fields(p, c->f, c->hm, c->omega_m, c->bw, c->parity, m, c->stream), "magnetic fields kernel");
+        return LBM_OK;
+    }
     CK(c, DISPATCH(c, launch_macroscopic, p, c->f, c->parity, kernel_force_kind(c), m, m + NL, m + 2 * NL, m + 3 * NL,
                    c->stream),
        "macroscopic kernel");
@@ -241,6 +252,19 @@ lbm_status do_steps(lbm_ctx* c, int nsteps, bool trace) {
     KParams p = make_params(c);
     const int fk = kernel_force_kind(c);
     lbm_status st;
+    if (c->hm) {
+        if (trace) return fail(c, LBM_ERR_UNSUPPORTED, "free streaming with the magnetic field");
+        if (c->force_kind != LBM_FORCE_NONE && c->force_kind != LBM_FORCE_UNIFORM)
+            return fail(c, LBM_ERR_UNSUPPORTED, "the magnetic field combines with no force or a uniform one only");
+        for (int s = 0; s < nsteps; ++s) {
+            if ((st = profile_mark(c, 0))) return st;
+            CK(c, launch_mhd_step(p, c->f, c->hm, c->omega_m, c->bw, c->parity, c->stream), "magnetic step kernel");
+            if ((st = profile_mark(c, 0))) return st;
+            c->parity ^= 1;
+            ++c->t;
+        }
+        return LBM_OK;
+    }
     for (int s = 0; s < nsteps; ++s) {
         if (!trace && c->force_kind == LBM_FORCE_SHAN_CHEN) {
             if ((st = profile_mark(c, 1))) return st;
@@ -260,6 +284,7 @@ void free_all(lbm_ctx* c) {
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     if (c->own_f && c->f) cudaFree(c->f);
+    cudaFree(c->hm);
     cudaFree(c->links);
     cudaFree(c->kolm);
     cudaFree(c->field);
@@ -333,6 +358,7 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
     if ((e = cudaMemsetAsync(c->flag_dev, 0, sizeof(unsigned int), c->stream)) != cudaSuccess)
         return bail(cuda_fail(c, e, "cudaMemset(flag)"));
 
+    c->has_mask = d->mask != nullptr;
     if (d->mask || d->walls_y) {
         if ((e = cudaMalloc(&c->links, sizeof(uint32_t) * c->N)) != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(links)"));
         uint8_t* dmask = nullptr;
@@ -408,6 +434,71 @@ lbm_status lbm_set_hermite_orders(lbm_ctx* c, int eq_order, int force_order) {
         return fail(c, LBM_ERR_UNSUPPORTED, "Hermite orders must be 2 or 6");
     c->eq_order = eq_order;
     c->force_order = force_order;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_magnetic(lbm_ctx* c, double eta, const double b_wall[3], const float* bx, const float* by,
+                            const float* bz) {
+    if (!c) return LBM_ERR_ARG;
+    if (c->storage != LBM_FP32) return fail(c, LBM_ERR_UNSUPPORTED, "the magnetic field needs FP32 storage");
+    if (c->slab) return fail(c, LBM_ERR_UNSUPPORTED, "the magnetic field is not offered on z slabs");
+    if (c->has_mask) return fail(c, LBM_ERR_UNSUPPORTED, "the magnetic field takes no solid mask");
+    if (c->force_kind != LBM_FORCE_NONE && c->force_kind != LBM_FORCE_UNIFORM)
+        return fail(c, LBM_ERR_UNSUPPORTED, "the magnetic field combines with no force or a uniform one only");
+    if (!(eta > 0.0)) return fail(c, LBM_ERR_ARG, "eta must be > 0");
+    if (c->parity) return fail(c, LBM_ERR_STATE, "set the magnetic field after an even number of steps");
+    const double om = 1.0 / (eta / 0.25 + 0.5);
+    if (!(om < 2.0)) return fail(c, LBM_ERR_ARG, "eta too small for a stable omega_m");
+    if (!c->hm) {
+        CK(c, cudaMalloc(&c->hm, sizeof(float) * 21 * c->N), "cudaMalloc(magnetic store)");
+        cudaFree(c->macro);  // the field buffer grows to 10 planes
+        c->macro = nullptr;
+    }
+    c->eta = eta;
+    c->omega_m = (float)om;
+    for (int a = 0; a < 3; ++a) c->bw[a] = b_wall ? (float)b_wall[a] : 0.0f;
+    lbm_status st = ensure_macro(c);
+    if (st) return st;
+    float* b3 = c->macro + 4 * c->NL;  // scratch: the b planes of the field buffer
+    const float* src[3] = {bx, by, bz};
+    for (int a = 0; a < 3; ++a) {
+        if (src[a]) CK(c, copy_in(b3 + a * c->NL, src[a], sizeof(float) * c->NL, c->stream), "magnetic field copy");
+        else CK(c, cudaMemsetAsync(b3 + a * c->NL, 0, sizeof(float) * c->NL, c->stream), "magnetic field clear");
+    }
+    KParams p = make_params(c);
+    CK(c, launch_mhd_init(p, c->f, c->hm, c->parity, b3, c->stream), "magnetic init kernel");
+    CK(c, cudaStreamSynchronize(c->stream), "magnetic init sync");
+    c->have_uprev = false;
+    return LBM_OK;
+}
+
+static lbm_status magnetic_copy(lbm_ctx* c, float* h, int to_buf) {
+    if (!c) return LBM_ERR_ARG;
+    if (!c->hm) return fail(c, LBM_ERR_STATE, "no magnetic field: call lbm_set_magnetic first");
+    if (!h) return fail(c, LBM_ERR_ARG, "h is NULL");
+    if (!to_buf && c->parity) return fail(c, LBM_ERR_STATE, "set magnetic populations after an even number of steps");
+    const size_t bytes = sizeof(float) * 21 * c->NL;
+    float* buf = h;
+    float* tmp = nullptr;
+    const bool dev = is_device_ptr(h);
+    if (!dev) {
+        CK(c, cudaMalloc(&tmp, bytes), "cudaMalloc(staging)");
+        buf = tmp;
+        if (!to_buf) {
+            cudaError_t e = cudaMemcpyAsync(tmp, h, bytes, cudaMemcpyHostToDevice, c->stream);
+            if (e != cudaSuccess) {
+                cudaFree(tmp);
+                return cuda_fail(c, e, "magnetic populations copy");
+            }
+        }
+    }
+    KParams p = make_params(c);
+    cudaError_t e = launch_mhd_copy(p, c->hm, c->bw, c->parity, buf, to_buf, c->stream);
+    if (e == cudaSuccess && !dev && to_buf) e = cudaMemcpyAsync(h, tmp, bytes, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "magnetic populations");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "magnetic populations sync");
     return LBM_OK;
 }
 
@@ -499,6 +590,21 @@ lbm_status lbm_macroscopic(lbm_ctx* c, float* rho, float* ux, float* uy, float* 
     float* outs[4] = {rho, ux, uy, uz};
     for (int k = 0; k < 4; ++k)
         if (outs[k]) CK(c, copy_out(outs[k], c->macro + k * c->NL, sizeof(float) * c->NL, c->stream), "macroscopic copy");
+    return sync_and_check(c);
+}
+
+lbm_status lbm_get_magnetic_populations(lbm_ctx* c, float* h) { return magnetic_copy(c, h, 1); }
+
+lbm_status lbm_set_magnetic_populations(lbm_ctx* c, const float* h) { return magnetic_copy(c, const_cast<float*>(h), 0); }
+
+lbm_status lbm_magnetic(lbm_ctx* c, float* bx, float* by, float* bz, float* jx, float* jy, float* jz) {
+    if (!c) return LBM_ERR_ARG;
+    if (!c->hm) return fail(c, LBM_ERR_STATE, "no magnetic field: call lbm_set_magnetic first");
+    lbm_status st = run_macro(c);
+    if (st) return st;
+    float* outs[6] = {bx, by, bz, jx, jy, jz};
+    for (int k = 0; k < 6; ++k)
+        if (outs[k]) CK(c, copy_out(outs[k], c->macro + (4 + k) * c->NL, sizeof(float) * c->NL, c->stream), "magnetic copy");
     return sync_and_check(c);
 }
 
@@ -602,6 +708,7 @@ struct CkptHeader {
 
 lbm_status lbm_save(lbm_ctx* c, const char* path) {
     if (!c || !path) return LBM_ERR_ARG;
+    if (c->hm) return fail(c, LBM_ERR_UNSUPPORTED, "checkpoint files hold the fluid store only");
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "CMLBMCK1", 8);
@@ -635,6 +742,7 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
 
 lbm_status lbm_load(lbm_ctx* c, const char* path) {
     if (!c || !path) return LBM_ERR_ARG;
+    if (c->hm) return fail(c, LBM_ERR_UNSUPPORTED, "checkpoint files hold the fluid store only");
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return fail(c, LBM_ERR_ARG, std::string("cannot open ") + path);
     CkptHeader h;

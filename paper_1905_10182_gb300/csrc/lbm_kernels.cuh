@@ -168,9 +168,7 @@ static cudaError_t launch_step_t(const KParams& p, S* f, int fk, bool trace, cud
     if constexpr (sizeof(S) == 2 && !LINKS) {
         // 16-bit storage, fully periodic, even nx, 4-byte aligned store: two nodes per thread
         if (!trace && p.nx % 2 == 0 && (reinterpret_cast<uintptr_t>(f) & 3) == 0) {
-            const uint32_t np = p.nx / 2, per = x2_pairs_per_block<ODD>(), per_sc = x2_pairs_per_block<true>();
-            const dim3 grid2((np + per - 1) / per, p.ny, p.nz - 2 * p.z0);
-            const dim3 grid_sc((np + per_sc - 1) / per_sc, p.ny, p.nz - 2 * p.z0);
+            const dim3 grid2 = x2_grid<ODD>(p), grid_sc = x2_grid<true>(p);
             switch (fk) {
             case FK_CONST: k_stream_collide_x2<S, ODD, FK_CONST, HO><<<grid2, X2_BLOCK, 0, st>>>(p, f); break;
             case FK_KOLMOGOROV: k_stream_collide_x2<S, ODD, FK_KOLMOGOROV, HO><<<grid2, X2_BLOCK, 0, st>>>(p, f); break;

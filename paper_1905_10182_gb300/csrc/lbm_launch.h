@@ -36,6 +36,16 @@ template <typename S>
 cudaError_t launch_halo_copy(const KParams& p, void* f, void* buf, int zs, int sz, int to_buf, int skip_blocked,
                              cudaStream_t st);
 
+// lbm_mhd.cu: the magnetic field of App. C (D3Q7, FP32 store hm[(3 l + a) N + n]) coupled to the
+// FP32 fluid store; fields: 10 planes of the caller's grid (rho, u, b, j)
+cudaError_t launch_mhd_step(const KParams& p, void* f, float* hm, float omega_m, const float bw[3], int odd,
+                            cudaStream_t st);
+cudaError_t launch_mhd_fields(const KParams& p, const void* f, float* hm, float omega_m, const float bw[3], int odd,
+                              float* out, cudaStream_t st);
+cudaError_t launch_mhd_init(const KParams& p, const void* f, float* hm, int odd, const float* b3, cudaStream_t st);
+cudaError_t launch_mhd_copy(const KParams& p, float* hm, const float bw[3], int odd, float* buf, int to_buf,
+                            cudaStream_t st);
+
 // lbm_reduce.cu: FP64 diagnostics over the macroscopic fields
 struct ReduceArgs {
     int nx, ny, nz;

@@ -206,31 +206,56 @@ __device__ __forceinline__ Macro2 collide_direct_x2(V2 (&g)[27], V2 Fx, V2 Fy, V
 }
 
 // ----------------------------------------------------------------------------- the kernel
-// Thread -> node pair (x0 = 2 pair, x0 + 1) of row (y, z) = (blockIdx.y, blockIdx.z + z0).
-// HALO (odd steps and the Shan-Chen stencil, which need the x neighbours): each warp owns 30
-// consecutive pairs; its lanes 0 and 31 take the pairs on either side (owned by the neighbouring
+// Thread -> node pair (x0 = 2 pair, x0 + 1) of a row (y, z).
+// HALO (odd steps and the Shan-Chen stencil, which need the x neighbours): warps are numbered over
+// all rows, wpr = ceil(np / 30) warps per row of np pairs; warp k of a row owns its pairs
+// 30k .. 30k + 29, and its lanes 0 and 31 take the pairs on either side (owned by the neighbouring
 // warps, wrapped periodically), so that every x neighbour of an owned pair is in the adjacent lane
 // and comes by a shuffle.  A halo lane computes only what its neighbour lane needs from it (node 1
-// of lane 0, node 0 of lane 31 are exact; the other node is not used) and stores nothing.
-// Otherwise (even steps without stencil) every lane owns one pair.  Lanes past the row end take a
-// wrapped pair and store nothing.
+// of lane 0, node 0 of lane 31 are exact; the other node is not used) and stores nothing; lanes
+// past the row end take a wrapped pair and store nothing.  Warps past the last row return whole.
+// Otherwise (even steps without stencil) every lane of a block row segment owns one pair.
+struct PairMap {
+    uint32_t pair, y, z;
+    bool owner, live;  // live: the warp maps to a row of the grid
+};
 template <bool HALO>
-__device__ __forceinline__ void map_pair(uint32_t np, uint32_t& pair, bool& owner) {
+__device__ __forceinline__ PairMap map_pair(const KParams& p) {
+    PairMap m;
+    const uint32_t np = (uint32_t)p.nx / 2;
     if (HALO) {
         const uint32_t lane = threadIdx.x & 31u;
-        const uint32_t qq = (blockIdx.x * (X2_BLOCK / 32) + (threadIdx.x >> 5)) * 30u + lane;  // pair + 1
-        owner = lane >= 1 && lane <= 30 && qq - 1 < np;
-        pair = qq == 0 ? np - 1 : (qq - 1) % np;
+        const uint32_t wpr = (np + 29u) / 30u;
+        const uint32_t W = blockIdx.x * (X2_BLOCK / 32) + (threadIdx.x >> 5);
+        const uint32_t row = W / wpr;
+        const uint32_t rows = (uint32_t)p.ny * (uint32_t)(p.nz - 2 * p.z0);
+        m.live = row < rows;
+        const uint32_t qq = (W - row * wpr) * 30u + lane;  // pair + 1 within the row
+        m.owner = m.live && lane >= 1 && lane <= 30 && qq - 1 < np;
+        m.pair = qq == 0 ? np - 1 : (qq - 1) % np;
+        m.y = row % (uint32_t)p.ny;
+        m.z = row / (uint32_t)p.ny + (uint32_t)p.z0;
     } else {
-        pair = blockIdx.x * X2_BLOCK + threadIdx.x;
-        owner = pair < np;
-        if (!owner) pair = np - 1;
+        m.pair = blockIdx.x * X2_BLOCK + threadIdx.x;
+        m.owner = m.pair < np;
+        m.live = true;
+        if (!m.owner) m.pair = np - 1;
+        m.y = blockIdx.y;
+        m.z = blockIdx.z + (uint32_t)p.z0;
     }
+    return m;
 }
-// pairs per block along x
+
+// launch grid of the pair kernel
 template <bool HALO>
-constexpr uint32_t x2_pairs_per_block() {
-    return HALO ? 30u * (X2_BLOCK / 32) : (uint32_t)X2_BLOCK;
+inline dim3 x2_grid(const KParams& p) {
+    const uint32_t np = (uint32_t)p.nx / 2;
+    const uint32_t rows_z = (uint32_t)(p.nz - 2 * p.z0);
+    if (HALO) {
+        const unsigned long long warps = (unsigned long long)((np + 29u) / 30u) * p.ny * rows_z;
+        return dim3((unsigned)((warps + X2_BLOCK / 32 - 1) / (X2_BLOCK / 32)), 1, 1);
+    }
+    return dim3((np + X2_BLOCK - 1) / X2_BLOCK, p.ny, rows_z);
 }
 
 // Element k * N + off of the store (plane k, node off; N < 2^31): one 32 x 32 -> 64-bit product.
@@ -280,11 +305,11 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5)) k_stream_collide_x2(K
     constexpr bool HALO = ODD || FK == FK_SHAN_CHEN;
     const unsigned full = 0xffffffffu;
     const uint32_t nx = p.nx, ny = p.ny, nz = p.nz;
-    uint32_t pair;
-    bool owner;
-    map_pair<HALO>(nx / 2, pair, owner);
-    const uint32_t x0 = 2 * pair;
-    const uint32_t y = blockIdx.y, z = blockIdx.z + p.z0;
+    const PairMap pm = map_pair<HALO>(p);
+    if (!pm.live) return;  // a whole warp past the last row
+    const bool owner = pm.owner;
+    const uint32_t x0 = 2 * pm.pair;
+    const uint32_t y = pm.y, z = pm.z;
     const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     const uint32_t yo[3] = {ym * nx, y * nx, yp * nx};
     const uint32_t pl = nx * ny;

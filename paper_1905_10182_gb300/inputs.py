@@ -86,6 +86,18 @@ def taylor_green(n, u0, rho0=1.0):
     return tuple(a.astype(np.float32) for a in (rho, ux, uy, uz))
 
 
+def orszag_tang(n, u0=0.0203, b0=0.0203):
+    """Initial velocity and magnetic field of the three-dimensional Orszag-Tang vortex on a periodic
+    2 pi box of n^3 nodes (x = 2 pi i / n), as printed in Sec. III:
+    u = u0 (2 sin y, 2 sin x, 0), b = 0.8 b0 (-2 sin 2y + sin z, 2 sin x + sin z, sin x + sin y).
+    Returns u, b, each (3, n, n, n) float32 indexed [component, z, y, x]."""
+    ax = 2.0 * math.pi * np.arange(n, dtype=np.float64) / n
+    z, y, x = np.meshgrid(ax, ax, ax, indexing="ij")
+    u = u0 * np.stack([2.0 * np.sin(y), 2.0 * np.sin(x), np.zeros_like(x)])
+    b = 0.8 * b0 * np.stack([-2.0 * np.sin(2.0 * y) + np.sin(z), 2.0 * np.sin(x) + np.sin(z), np.sin(x) + np.sin(y)])
+    return u.astype(np.float32), b.astype(np.float32)
+
+
 def sphere_pack(nx, ny, nz, seed, phi_max=0.2, rmin=3, rmax=8, max_tries=2000):
     """Random non-overlapping spheres (radii uniform in [rmin, rmax], centres uniform, rejection
     on overlap) added until the solid fraction reaches a target drawn uniformly in [0, phi_max].

@@ -135,6 +135,32 @@ class Solver:
         self._check(self._lib.lbm_macroscopic(self._h, *(nat.ptr(a) for a in (rho, ux, uy, uz))))
         return rho, ux, uy, uz
 
+    # -- magnetic field (App. C)
+    def set_magnetic(self, eta, b=None, b_wall=(0.0, 0.0, 0.0)):
+        """Turns on the D3Q7 magnetic field: b = (bx, by, bz) arrays of the grid's shape (None: zero)
+        or a constant 3-vector; b_wall is held at the y walls."""
+        if b is not None and all(np.isscalar(v) for v in b):
+            b = [np.full(self.shape, float(v), dtype=np.float32) for v in b]
+        self._keep_b = [None, None, None] if b is None else [_f32(a) for a in b]
+        bw = (ctypes.c_double * 3)(*[float(v) for v in b_wall])
+        self._check(self._lib.lbm_set_magnetic(self._h, float(eta), bw, *(nat.ptr(a) for a in self._keep_b)))
+
+    def get_magnetic_populations(self, out=None):
+        if out is None:
+            out = np.empty((21,) + self.shape, dtype=np.float32)
+        self._check(self._lib.lbm_get_magnetic_populations(self._h, nat.ptr(out)))
+        return out
+
+    def set_magnetic_populations(self, h):
+        h = _f32(h)
+        self._check(self._lib.lbm_set_magnetic_populations(self._h, nat.ptr(h)))
+
+    def magnetic(self):
+        """b and j = curl b (each (3,) + shape, float32) at the current time."""
+        out = [np.empty(self.shape, dtype=np.float32) for _ in range(6)]
+        self._check(self._lib.lbm_magnetic(self._h, *(nat.ptr(a) for a in out)))
+        return np.stack(out[:3]), np.stack(out[3:])
+
     def stats(self):
         out = (ctypes.c_double * nat.LBM_STATS_LEN)()
         self._check(self._lib.lbm_stats(self._h, out))
@@ -178,6 +204,10 @@ class Solver:
     @property
     def time(self):
         return self._lib.lbm_time(self._h)
+
+
+# launch schedules of the batched step (lbm_batch_set_shape)
+SCHEDULES = ("strided", "contiguous", "strided_prefetch")
 
 
 class BatchSolver:
@@ -243,9 +273,15 @@ class BatchSolver:
         return self._lib.lbm_batch_time(self._h)
 
     def autotune(self, trial_steps=20):
-        out = (ctypes.c_double * 3)()
+        out = (ctypes.c_double * 4)()
         self._check(self._lib.lbm_batch_autotune(self._h, int(trial_steps), out))
-        return dict(mlups=out[0], tile=int(out[1]), blocks_per_sm=int(out[2]))
+        return dict(mlups=out[0], tile=int(out[1]), blocks_per_sm=int(out[2]),
+                    schedule=SCHEDULES[int(out[3])])
+
+    def set_shape(self, tile, blocks_per_sm, schedule="strided"):
+        """Launch shape without tuning (tile: nodes per tile; blocks_per_sm 0: one block per tile)."""
+        sch = SCHEDULES.index(schedule) if isinstance(schedule, str) else int(schedule)
+        self._check(self._lib.lbm_batch_set_shape(self._h, int(tile), int(blocks_per_sm), sch))
 
     def step(self, nsteps=1):
         self._check(self._lib.lbm_batch_step(self._h, int(nsteps)))

@@ -98,3 +98,19 @@ def test_batch_autotune_resets_to_rest():
     s.set_force("uniform", doms[1]["force"])
     s.step(7)
     assert np.array_equal(b.get_populations(1), s.get_populations())
+
+
+@pytest.mark.parametrize("shape", [(64, 0, "strided"), (128, 2, "strided"), (128, 1, "contiguous"),
+                                   (256, 4, "contiguous"), (64, 8, "strided_prefetch"), (128, 1, "strided_prefetch")])
+def test_batch_launch_shapes_bit_identical(shape):
+    """Every launch shape and schedule (strided, contiguous runs or strided with L2 prefetch) gives the same
+    populations, bit for bit, as the single-domain solver."""
+    doms = _domains()
+    b = BatchSolver(doms)
+    b.set_shape(*shape)
+    b.step(9)
+    for k, d in enumerate(doms):
+        s = Solver(d["nx"], d["ny"], d["nz"], nu=d["nu"], walls_y=d["walls_y"], mask=d["mask"])
+        s.set_force("uniform", d["force"])
+        s.step(9)
+        assert np.array_equal(b.get_populations(k), s.get_populations()), (shape, k)
