@@ -56,6 +56,12 @@ class _Desc(ctypes.Structure):
     ]
 
 
+class _CG(ctypes.Structure):
+    _fields_ = [("grid", ctypes.POINTER(_Desc)), ("rho_r0", ctypes.c_double), ("rho_b0", ctypes.c_double),
+                ("nu_r", ctypes.c_double), ("nu_b", ctypes.c_double), ("A", ctypes.c_double),
+                ("beta", ctypes.c_double), ("gvec", ctypes.c_double * 3)]
+
+
 _lib = None
 
 
@@ -103,6 +109,18 @@ def lib():
         L.orc_mhd_step.restype = ctypes.c_int
         L.orc_mhd_fields.argtypes = [ctypes.POINTER(_Desc), ctypes.c_double, dp, dp, dp, dp, dp, dp]
         L.orc_mhd_fields.restype = ctypes.c_int
+        L.orc_cg_phi.argtypes = [ctypes.c_double, dp]
+        L.orc_cg_equilibrium.argtypes = [ctypes.c_double, dp, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.orc_cg_perturbation.argtypes = [ctypes.c_double, dp, dp]
+        L.orc_cg_recolour.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp,
+                                      dp, dp]
+        for name in ("orc_cg_init",):
+            getattr(L, name).argtypes = [ctypes.POINTER(_CG), dp, dp, dp, dp, dp]
+            getattr(L, name).restype = ctypes.c_int
+        L.orc_cg_step.argtypes = [ctypes.POINTER(_CG), dp, dp, ctypes.c_int]
+        L.orc_cg_step.restype = ctypes.c_int
+        L.orc_cg_fields.argtypes = [ctypes.POINTER(_CG), dp, dp, dp, dp, dp]
+        L.orc_cg_fields.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -344,6 +362,68 @@ class MhdGrid(Grid):
         self._check(lib().orc_mhd_fields(ctypes.byref(self.desc), self.omega_m, _dp(f), _dp(h), _dp(rho), _dp(u),
                                          _dp(b), _dp(j)), "mhd_fields")
         return rho, u, b, j
+
+
+# --------------------------------------------------------------------------- colour gradient (App. D)
+def cg_phi(alpha) -> np.ndarray:
+    out = np.zeros(Q)
+    lib().orc_cg_phi(float(alpha), _dp(out))
+    return out
+
+
+def cg_equilibrium(rho, u, alpha, nu, grad_rho=(0.0, 0.0, 0.0)) -> np.ndarray:
+    out = np.zeros(Q)
+    lib().orc_cg_equilibrium(float(rho), _dp(_vec(u)), float(alpha), float(nu), _dp(_vec(grad_rho)), _dp(out))
+    return out
+
+
+def cg_perturbation(A, grad_phi) -> np.ndarray:
+    out = np.zeros(Q)
+    lib().orc_cg_perturbation(float(A), _dp(_vec(grad_phi)), _dp(out))
+    return out
+
+
+def cg_recolour(beta, rho_r, rho_b, alpha, grad_phi, fs):
+    fr, fb = np.zeros(Q), np.zeros(Q)
+    lib().orc_cg_recolour(float(beta), float(rho_r), float(rho_b), float(alpha), _dp(_vec(grad_phi)),
+                          _dp(_vec(fs, Q)), _dp(fr), _dp(fb))
+    return fr, fb
+
+
+class CgGrid(Grid):
+    """Two-colour populations (fr, fb, each (27, nz, ny, nx)) of the colour-gradient model (App. D)."""
+
+    def __init__(self, nx, ny, nz, rho_r0, rho_b0, nu_r, nu_b, A=0.0, beta=0.7, gvec=(0.0, 0.0, 0.0), **kw):
+        super().__init__(nx, ny, nz, nu=nu_r, **kw)
+        m = _CG()
+        m.grid = ctypes.pointer(self.desc)
+        m.rho_r0, m.rho_b0, m.nu_r, m.nu_b = float(rho_r0), float(rho_b0), float(nu_r), float(nu_b)
+        m.A, m.beta = float(A), float(beta)
+        for k in range(3):
+            m.gvec[k] = float(gvec[k])
+        self.cg = m
+
+    def cg_init(self, rho_r, rho_b, u=None):
+        rr = np.ascontiguousarray(np.broadcast_to(np.asarray(rho_r, np.float64), self.shape)).reshape(-1)
+        rb = np.ascontiguousarray(np.broadcast_to(np.asarray(rho_b, np.float64), self.shape)).reshape(-1)
+        uu = np.zeros((3, self.N)) if u is None else np.ascontiguousarray(np.asarray(u, np.float64).reshape(3, -1))
+        fr, fb = np.zeros((Q,) + self.shape), np.zeros((Q,) + self.shape)
+        self._check(lib().orc_cg_init(ctypes.byref(self.cg), _dp(rr), _dp(rb), _dp(uu), _dp(fr), _dp(fb)), "cg_init")
+        return fr, fb
+
+    def cg_step(self, fr, fb, nsteps=1):
+        fr = np.ascontiguousarray(fr, dtype=np.float64).copy()
+        fb = np.ascontiguousarray(fb, dtype=np.float64).copy()
+        self._check(lib().orc_cg_step(ctypes.byref(self.cg), _dp(fr), _dp(fb), int(nsteps)), "cg_step")
+        return fr, fb
+
+    def cg_fields(self, fr, fb):
+        fr = np.ascontiguousarray(fr, dtype=np.float64)
+        fb = np.ascontiguousarray(fb, dtype=np.float64)
+        rr, rb = np.zeros(self.shape), np.zeros(self.shape)
+        u = np.zeros((3,) + self.shape)
+        self._check(lib().orc_cg_fields(ctypes.byref(self.cg), _dp(fr), _dp(fb), _dp(rr), _dp(rb), _dp(u)), "cg_fields")
+        return rr, rb, u
 
 
 # --------------------------------------------------------------------------- diagnostics

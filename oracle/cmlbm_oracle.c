@@ -825,3 +825,239 @@ int orc_mhd_fields(const orc_desc* d, double omega_m, const double* f, const dou
     }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ colour gradient (App. D) */
+static int shell(int i) { return CX[i] * CX[i] + CY[i] * CY[i] + CZ[i] * CZ[i]; }
+
+void orc_cg_phi(double alpha, double phi_i[Q]) {
+    for (int i = 0; i < Q; ++i) {
+        switch (shell(i)) {
+        case 0: phi_i[i] = alpha; break;
+        case 1: phi_i[i] = 2.0 * (1.0 - alpha) / 19.0; break;
+        case 2: phi_i[i] = (1.0 - alpha) / 38.0; break;
+        default: phi_i[i] = (1.0 - alpha) / 152.0; break;
+        }
+    }
+}
+
+void orc_cg_equilibrium(double rho, const double u[3], double alpha, double nu, const double grad_rho[3],
+                        double feq[Q]) {
+    double phi_i[Q], fc[Q];
+    orc_cg_phi(alpha, phi_i);
+    orc_equilibrium(rho, u, 6, fc);
+    const double ug = u[0] * grad_rho[0] + u[1] * grad_rho[1] + u[2] * grad_rho[2];
+    for (int i = 0; i < Q; ++i) {
+        /* G : c c with G = (u grad rho + grad rho u) / 48 */
+        const double cu = CX[i] * u[0] + CY[i] * u[1] + CZ[i] * u[2];
+        const double cg = CX[i] * grad_rho[0] + CY[i] * grad_rho[1] + CZ[i] * grad_rho[2];
+        const double Gcc = 2.0 * cu * cg / 48.0;
+        double Phi;
+        switch (shell(i)) {
+        case 0: Phi = -3.0 * nu * ug; break;
+        case 1: Phi = 16.0 * nu * Gcc; break;
+        case 2: Phi = 4.0 * nu * Gcc; break;
+        default: Phi = nu * Gcc; break;
+        }
+        feq[i] = rho * phi_i[i] + (fc[i] - rho * weight(i)) + Phi;
+    }
+}
+
+void orc_cg_perturbation(double A, const double gp[3], double out[Q]) {
+    const double g2 = gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2];
+    for (int i = 0; i < Q; ++i) out[i] = 0.0;
+    if (!(g2 > 0.0)) return;
+    const double gn = sqrt(g2);
+    for (int i = 0; i < Q; ++i) {
+        const double cg = CX[i] * gp[0] + CY[i] * gp[1] + CZ[i] * gp[2];
+        double B;
+        switch (shell(i)) {
+        case 0: B = -10.0 / 27.0; break;
+        case 1: B = 2.0 / 27.0; break;
+        case 2: B = 1.0 / 54.0; break;
+        default: B = 1.0 / 216.0; break;
+        }
+        out[i] = 0.5 * A * gn * (weight(i) * cg * cg / g2 - B);
+    }
+}
+
+void orc_cg_recolour(double beta, double rho_r, double rho_b, double alpha, const double gp[3], const double fs[Q],
+                     double fr[Q], double fb[Q]) {
+    const double rho = rho_r + rho_b;
+    double phi_i[Q];
+    orc_cg_phi(alpha, phi_i);
+    const double gn = sqrt(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2]);
+    for (int i = 0; i < Q; ++i) {
+        double cosv = 0.0;
+        if (gn > 0.0 && shell(i) > 0)
+            cosv = (CX[i] * gp[0] + CY[i] * gp[1] + CZ[i] * gp[2]) / (sqrt((double)shell(i)) * gn);
+        fr[i] = rho_r / rho * fs[i] + beta * rho_r * rho_b / (rho * rho) * cosv * rho * phi_i[i];
+        fb[i] = fs[i] - fr[i];
+    }
+}
+
+static double cg_order(const orc_cg* m, double rr, double rb) {
+    const double a = rr / m->rho_r0, b = rb / m->rho_b0;
+    return (a - b) / (a + b);
+}
+
+static void cg_params(const orc_cg* m, double phi, double* alpha, double* nu) {
+    const double ab = 8.0 / 27.0;
+    const double ar = 1.0 - (1.0 - ab) * m->rho_b0 / m->rho_r0;
+    *alpha = 0.5 * (1.0 + phi) * ar + 0.5 * (1.0 - phi) * ab;
+    *nu = 1.0 / (0.5 * (1.0 + phi) / m->nu_r + 0.5 * (1.0 - phi) / m->nu_b);
+}
+
+/* isotropic central gradient of a node field; a neighbour behind a wall takes the node's value */
+static void cg_gradient(const orc_desc* d, const double* X, int x, int y, int z, double g[3]) {
+    const long long n = node_index(d, x, y, z);
+    g[0] = g[1] = g[2] = 0.0;
+    for (int i = 1; i < Q; ++i) {
+        long long mnb = neighbour(d, x, y, z, i, +1);
+        const double v = mnb >= 0 ? X[mnb] : X[n];
+        g[0] += weight(i) * CX[i] * v / CS2;
+        g[1] += weight(i) * CY[i] * v / CS2;
+        g[2] += weight(i) * CZ[i] * v / CS2;
+    }
+}
+
+static int check_cg(const orc_cg* m) {
+    if (!m || !m->grid) return ORC_ERR_ARG;
+    if (!(m->rho_r0 > 0.0) || !(m->rho_b0 > 0.0) || !(m->nu_r > 0.0) || !(m->nu_b > 0.0)) return ORC_ERR_ARG;
+    if (m->grid->mask) return ORC_ERR_ARG;
+    return check_desc(m->grid);
+}
+
+int orc_cg_init(const orc_cg* m, const double* rho_r, const double* rho_b, const double* u3, double* fr, double* fb) {
+    int st = check_cg(m);
+    if (st) return st;
+    const orc_desc* d = m->grid;
+    long long N = (long long)d->nx * d->ny * d->nz;
+#pragma omp parallel for schedule(static)
+    for (long long n = 0; n < N; ++n) {
+        const double rr = rho_r[n], rb = rho_b[n], rho = rr + rb;
+        double alpha, nu, feq[Q], u[3] = {u3[n], u3[N + n], u3[2 * N + n]}, g0[3] = {0, 0, 0};
+        cg_params(m, cg_order(m, rr, rb), &alpha, &nu);
+        orc_cg_equilibrium(rho, u, alpha, nu, g0, feq);
+        for (int i = 0; i < Q; ++i) {
+            fr[(long long)i * N + n] = rr / rho * feq[i];
+            fb[(long long)i * N + n] = rb / rho * feq[i];
+        }
+    }
+    return ORC_OK;
+}
+
+/* per-node fields of the current state: rho_r, rho_b, rho, phi */
+static void cg_node_fields(const orc_cg* m, const double* fr, const double* fb, long long N, double* rr, double* rb,
+                           double* rho, double* phi) {
+#pragma omp parallel for schedule(static)
+    for (long long n = 0; n < N; ++n) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            a += fr[(long long)i * N + n];
+            b += fb[(long long)i * N + n];
+        }
+        rr[n] = a;
+        rb[n] = b;
+        rho[n] = a + b;
+        phi[n] = cg_order(m, a, b);
+    }
+}
+
+static void cg_force(const orc_cg* m, double rho, double F[3]) {
+    const double dr = rho - 0.5 * (m->rho_r0 + m->rho_b0);
+    F[0] = dr * m->gvec[0];
+    F[1] = dr * m->gvec[1];
+    F[2] = dr * m->gvec[2];
+}
+
+int orc_cg_step(const orc_cg* m, double* fr, double* fb, int nsteps) {
+    int st = check_cg(m);
+    if (st) return st;
+    const orc_desc* d = m->grid;
+    long long N = (long long)d->nx * d->ny * d->nz;
+    double* frs = (double*)malloc(sizeof(double) * Q * N);
+    double* fbs = (double*)malloc(sizeof(double) * Q * N);
+    double* fld = (double*)malloc(sizeof(double) * 4 * N);
+    if (!frs || !fbs || !fld) {
+        free(frs);
+        free(fbs);
+        free(fld);
+        return ORC_ERR_NOMEM;
+    }
+    double *rr = fld, *rb = fld + N, *rhof = fld + 2 * N, *phif = fld + 3 * N;
+    int err = ORC_OK;
+    for (int s = 0; s < nsteps && !err; ++s) {
+        cg_node_fields(m, fr, fb, N, rr, rb, rhof, phif);
+#pragma omp parallel for schedule(static) reduction(| : err)
+        for (int z = 0; z < d->nz; ++z)
+            for (int y = 0; y < d->ny; ++y)
+                for (int x = 0; x < d->nx; ++x) {
+                    const long long n = node_index(d, x, y, z);
+                    double f[Q], F[3], gphi[3], grho[3], alpha, nu, rho, u[3], feq[Q], Fi[Q], k[Q], keq[Q], R[Q],
+                        ks[Q], fs[Q], pert[Q], ofr[Q], ofb[Q], L[Q];
+                    for (int i = 0; i < Q; ++i) f[i] = fr[(long long)i * N + n] + fb[(long long)i * N + n];
+                    cg_force(m, rhof[n], F);
+                    macroscopic_node(f, F, &rho, u);
+                    cg_gradient(d, phif, x, y, z, gphi);
+                    cg_gradient(d, rhof, x, y, z, grho);
+                    cg_params(m, phif[n], &alpha, &nu);
+                    /* single phase (App. D): the CM collision of Sec. II with the enhanced equilibrium */
+                    orc_cg_equilibrium(rho, u, alpha, nu, grho, feq);
+                    orc_forcing_term(F, u, 6, Fi);
+                    paper_lambda(1.0 / (3.0 * nu + 0.5), L);
+                    orc_central_moments(u, f, k);
+                    orc_central_moments(u, feq, keq);
+                    orc_central_moments(u, Fi, R);
+                    for (int j = 0; j < Q; ++j) ks[j] = (1.0 - L[j]) * k[j] + L[j] * keq[j] + (1.0 - 0.5 * L[j]) * R[j];
+                    orc_inverse_fast(u, ks, fs); /* equals the literal solve (pinned) */
+                    /* perturbation, then recolouring */
+                    orc_cg_perturbation(m->A, gphi, pert);
+                    for (int i = 0; i < Q; ++i) fs[i] += pert[i];
+                    orc_cg_recolour(m->beta, rr[n], rb[n], alpha, gphi, fs, ofr, ofb);
+                    for (int i = 0; i < Q; ++i) {
+                        frs[(long long)i * N + n] = ofr[i];
+                        fbs[(long long)i * N + n] = ofb[i];
+                    }
+                }
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < d->nz; ++z)
+            for (int y = 0; y < d->ny; ++y)
+                for (int x = 0; x < d->nx; ++x) {
+                    const long long n = node_index(d, x, y, z);
+                    for (int i = 0; i < Q; ++i) {
+                        const long long src = neighbour(d, x, y, z, i, -1);
+                        const long long a = (long long)i * N, o = (long long)orc_opposite(i) * N;
+                        fr[a + n] = src >= 0 ? frs[a + src] : frs[o + n];
+                        fb[a + n] = src >= 0 ? fbs[a + src] : fbs[o + n];
+                    }
+                }
+    }
+    free(frs);
+    free(fbs);
+    free(fld);
+    return err;
+}
+
+int orc_cg_fields(const orc_cg* m, const double* fr, const double* fb, double* rho_r, double* rho_b, double* u3) {
+    int st = check_cg(m);
+    if (st) return st;
+    const orc_desc* d = m->grid;
+    long long N = (long long)d->nx * d->ny * d->nz;
+#pragma omp parallel for schedule(static)
+    for (long long n = 0; n < N; ++n) {
+        double f[Q], F[3], rho, u[3], a = 0.0, b = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            a += fr[(long long)i * N + n];
+            b += fb[(long long)i * N + n];
+            f[i] = fr[(long long)i * N + n] + fb[(long long)i * N + n];
+        }
+        cg_force(m, a + b, F);
+        macroscopic_node(f, F, &rho, u);
+        rho_r[n] = a;
+        rho_b[n] = b;
+        u3[n] = u[0];
+        u3[N + n] = u[1];
+        u3[2 * N + n] = u[2];
+    }
+    return ORC_OK;
+}

@@ -133,6 +133,52 @@ int orc_mhd_step(const orc_desc* d, double omega_m, const double b_wall[3], doub
 int orc_mhd_fields(const orc_desc* d, double omega_m, const double* f, const double* h, double* rho, double* u3,
                    double* b3, double* j3);
 
+/* ------------------------------------------------------------------ colour gradient (App. D)
+ * Two immiscible fluids, red and blue, with D3Q27 populations fr, fb (full populations, layout of
+ * f); the total f = fr + fb takes the central-moment collision of Sec. II with an enhanced
+ * equilibrium, then a perturbation (interfacial tension) and a recolouring step split it again.
+ * Per node (readings where App. D is silent or garbled):
+ *   rho_k = sum fk, rho = rho_r + rho_b, rho u = sum f c + F/2,
+ *   phi = (rho_r/rho_r0 - rho_b/rho_b0) / (rho_r/rho_r0 + rho_b/rho_b0),
+ *   alpha_b = 8/27, alpha_r = 1 - (1 - alpha_b) rho_b0 / rho_r0, alpha = ((1+phi) alpha_r + (1-phi) alpha_b)/2,
+ *   1/nu = (1+phi)/(2 nu_r) + (1-phi)/(2 nu_b), omega = 1/(3 nu + 1/2) on k4..k8;
+ *   gradients grad X = (1/cs^2) sum_i w_i c_i X(x + c_i), a missing neighbour behind a wall
+ *   taking the node's own value;
+ *   f^eq_i = rho phi_i(alpha) + (f^eq,complete_i(rho, u) - rho w_i) + Phi_i (the enhanced
+ *   equilibrium of App. D: the sixth-order Hermite terms of Eq. eq:truncation without their
+ *   zeroth-order term), Phi_i from G = (u grad rho + grad rho u) / 48;
+ *   single phase: k* = (I - L) k + L k^eq + (I - L/2) R, f* = (T^T)^-1 k* (R: the complete
+ *   forcing term of Eq. generalForcing);
+ *   perturbation: f* += (A/2)|grad phi| [w_i (c_i . grad phi)^2 / |grad phi|^2 - B_i] (squared, so
+ *   that it conserves mass);
+ *   recolouring: fr*_i = (rho_r/rho) f*_i + beta rho_r rho_b / rho^2 cos(theta_i) rho phi_i(alpha),
+ *   fb*_i = f*_i - fr*_i, cos(theta_i) = c_i . grad phi / (|c_i| |grad phi|);
+ *   body force (Sec. III, Rayleigh-Taylor): F = (rho - (rho_r0 + rho_b0)/2) gvec. */
+typedef struct {
+    const orc_desc* grid;  /* nx, ny, nz, walls_y, threads (collision, force and mask fields unused) */
+    double rho_r0, rho_b0; /* reference densities of the pure fluids */
+    double nu_r, nu_b;
+    double A;              /* perturbation amplitude */
+    double beta;           /* recolouring parameter */
+    double gvec[3];        /* gravity vector of the body force */
+} orc_cg;
+/* phi_i(alpha) of App. D */
+void orc_cg_phi(double alpha, double phi_i[ORC_Q]);
+/* enhanced equilibrium */
+void orc_cg_equilibrium(double rho, const double u[3], double alpha, double nu, const double grad_rho[3],
+                        double feq[ORC_Q]);
+/* perturbation operator values */
+void orc_cg_perturbation(double A, const double grad_phi[3], double out[ORC_Q]);
+/* recolouring of the post-collision total fs into fr, fb */
+void orc_cg_recolour(double beta, double rho_r, double rho_b, double alpha, const double grad_phi[3],
+                     const double fs[ORC_Q], double fr[ORC_Q], double fb[ORC_Q]);
+/* initial state: fk_i = (rho_k / rho) f^eq_i(rho, u) with the enhanced equilibrium at alpha(phi)
+   and no density-gradient term */
+int orc_cg_init(const orc_cg* m, const double* rho_r, const double* rho_b, const double* u3, double* fr, double* fb);
+int orc_cg_step(const orc_cg* m, double* fr, double* fb, int nsteps);
+/* rho_r, rho_b (N each), u (3N) */
+int orc_cg_fields(const orc_cg* m, const double* fr, const double* fb, double* rho_r, double* rho_b, double* u3);
+
 #ifdef __cplusplus
 }
 #endif
