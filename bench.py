@@ -44,7 +44,25 @@ WORKLOADS = {
     "orszag_tang128": dict(n=128, kind="mhd", nu=0.005, eta=0.005, u0=0.0203, b0=0.0203,
                            text="3D Orszag-Tang vortex 128^3 periodic (magnetic field on D3Q7, Lorentz force "
                                 "j x b), u0=b0=0.0203, nu=eta=0.005"),
+    "rayleigh_taylor64": dict(n=64, kind="cg", nu=0.005, rho_h=3.0, rho_l=1.0, A=1e-4, beta=0.7,
+                              text="Rayleigh-Taylor instability, colour-gradient two-phase model, 64x256x64 "
+                                   "(W=64, walls in y), At=0.5, Re=512, sqrt(gW)=0.04"),
 }
+# two-phase step, algorithmic bytes: both colours read and written once (432 + 432 B) and the
+# phase fields written and read back (8 + 8 B).  The field pass reads the colours a second time
+# (432 B), a cost of this two-pass design that is not counted.
+CG_BYTES_PER_NODE = 880
+
+
+def grid_shape(wl):
+    n = wl["n"]
+    return (n, 4 * n, n) if wl["kind"] == "cg" else (n, n, n)
+
+
+def cg_params(wl):
+    g = 0.04 ** 2 / wl["n"]
+    return dict(rho_r0=wl["rho_h"], rho_b0=wl["rho_l"], nu_r=wl["nu"], nu_b=wl["nu"], A=wl["A"], beta=wl["beta"],
+                g=(0.0, -g, 0.0))
 # bytes per node of one step, AA in place: 27 populations read + written (+ 21 magnetic ones)
 MHD_BYTES_PER_NODE = 216 + 168
 
@@ -121,6 +139,18 @@ def oracle_grid(wl, m, threads):
         kw.update(force_kind=oracle.FORCE_SHAN_CHEN, G=wl["G"])
     elif wl["kind"] == "kolmogorov":
         kw.update(force_kind=oracle.FORCE_KOLMOGOROV, force=(wl["F0"], 0, 0))
+    if wl["kind"] == "cg":
+        from paper_1905_10182_gb300 import rayleigh_taylor
+        rr, rb = rayleigh_taylor.initial_densities(m, wl["rho_h"], wl["rho_l"])
+        prm = cg_params(sub)
+        cg = oracle.CgGrid(m, 4 * m, m, rho_r0=prm["rho_r0"], rho_b0=prm["rho_b0"], nu_r=prm["nu_r"],
+                           nu_b=prm["nu_b"], A=prm["A"], beta=prm["beta"], gvec=prm["g"], walls_y=True,
+                           threads=threads)
+        state = list(cg.cg_init(rr.astype(np.float64), rb.astype(np.float64)))
+
+        def step(k):
+            state[0], state[1] = cg.cg_step(state[0], state[1], k)
+        return step
     if wl["kind"] == "mhd":
         g = oracle.MhdGrid(m, m, m, eta=wl["eta"], **kw)
         f = g.init_equilibrium(rho.astype(np.float64), u)
@@ -201,6 +231,8 @@ def oracle_mlups(wl, target_s=12.0, threads=None):
     n = wl["n"]
     # a 512^3 FP64 oracle state (29 GB x 2) does not fit a bounded sample: use a 128^3 box
     sample_n = min(n, 128)
+    if wl["kind"] == "cg":
+        sample_n = min(n, 16)
     step = oracle_grid(wl, sample_n, threads)
     t0 = time.perf_counter()
     step(1)
@@ -209,10 +241,12 @@ def oracle_mlups(wl, target_s=12.0, threads=None):
     t0 = time.perf_counter()
     step(steps)
     dt = time.perf_counter() - t0
-    nodes = sample_n ** 3
+    shape = grid_shape(dict(wl, n=sample_n))
+    nodes = shape[0] * shape[1] * shape[2]
     return {"value": nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-            "sample": f"{steps} oracle steps (FP64, five-step algorithm of Sec. II) on a {sample_n}^3 "
-                      f"{'box of the ' if sample_n != n else ''}{wl['kind']} state, {dt:.1f} s"}
+            "sample": f"{steps} oracle steps (FP64, five-step algorithm of Sec. II) on a "
+                      f"{'x'.join(map(str, shape))} {'box of the ' if sample_n != n else ''}{wl['kind']} state, "
+                      f"{dt:.1f} s"}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -231,18 +265,22 @@ def run_reference(args, wl):
     per_node = 1.0 / (probe["value"] * 1e6)
     budget = args.budget_s / max(1, args.steps + args.warmup)
     m = int(max(8, min(wl["n"], (budget / per_node) ** (1.0 / 3.0))))
+    if wl["kind"] == "cg":
+        m = max(8, int(m / 4 ** (1.0 / 3.0)))  # the box is m x 4m x m
     step = oracle_grid(wl, m, threads)
     step(args.warmup)
     t0 = time.perf_counter()
     step(args.steps)
     dt = time.perf_counter() - t0
-    val = m ** 3 * args.steps / dt / 1e6
+    shape = grid_shape(dict(wl, n=m))
+    val = shape[0] * shape[1] * shape[2] * args.steps / dt / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["text"] + f"; oracle sample box {m}^3 per step", "nodes_per_step": m ** 3},
+            "config": {"workload": wl["text"] + f"; oracle sample box {'x'.join(map(str, shape))} per step",
+                       "nodes_per_step": shape[0] * shape[1] * shape[2]},
             "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-                             "sample": f"{args.steps} timed oracle steps on an {m}^3 box of the workload"},
+                             "sample": f"{args.steps} timed oracle steps on a {'x'.join(map(str, shape))} box of the workload"},
             "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
@@ -382,18 +420,29 @@ def run_ours(args, wl):
     build()
 
     n = wl["n"]
-    nodes = n ** 3
-    rho, ux, uy, uz = initial_fields(wl)
+    shape = grid_shape(wl)
+    nodes = shape[0] * shape[1] * shape[2]
+    cg = wl["kind"] == "cg"
+    if cg:
+        from paper_1905_10182_gb300 import rayleigh_taylor
+        rho_r, rho_b = rayleigh_taylor.initial_densities(n, wl["rho_h"], wl["rho_l"])
+        rho = rho_r + rho_b
+        ux = uy = uz = np.zeros_like(rho)
+    else:
+        rho, ux, uy, uz = initial_fields(wl)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
     # ---- device-resident run (value, roofline)
-    s = Solver(n, n, n, nu=wl["nu"], storage=args.storage)
+    s = Solver(*shape, nu=wl["nu"], storage=args.storage, walls_y=cg)
     configure_force(s, wl)
-    s.set_state(torch.from_numpy(rho).cuda(), torch.from_numpy(ux).cuda(), torch.from_numpy(uy).cuda(),
-                torch.from_numpy(uz).cuda())
+    if cg:
+        s.set_colour_gradient(torch.from_numpy(rho_r).cuda(), torch.from_numpy(rho_b).cuda(), **cg_params(wl))
+    else:
+        s.set_state(torch.from_numpy(rho).cuda(), torch.from_numpy(ux).cuda(), torch.from_numpy(uy).cuda(),
+                    torch.from_numpy(uz).cuda())
     mhd = wl["kind"] == "mhd"
     if mhd:
         bmag = initial_magnetic(wl)
@@ -428,15 +477,18 @@ def run_ours(args, wl):
     del s
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    pin = [torch.from_numpy(a).pin_memory() for a in (rho, ux, uy, uz)]
+    pin = [torch.from_numpy(a).pin_memory() for a in ((rho_r, rho_b) if cg else (rho, ux, uy, uz))]
     pin_b = [torch.from_numpy(a).pin_memory() for a in bmag] if mhd else None
     out = [torch.empty(a.shape, dtype=torch.float32).pin_memory() for a in (rho, ux, uy, uz)]
-    e = Solver(n, n, n, nu=wl["nu"], storage=args.storage)
+    e = Solver(*shape, nu=wl["nu"], storage=args.storage, walls_y=cg)
     configure_force(e, wl)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    e.set_state(*pin)
+    if cg:
+        e.set_colour_gradient(*pin, **cg_params(wl))
+    else:
+        e.set_state(*pin)
     if mhd:
         e.set_magnetic(wl["eta"], b=pin_b)
     e.step(args.steps)
@@ -450,10 +502,11 @@ def run_ours(args, wl):
         t_e2e = float(t.item())
     e.close()
     e2e = {"value": world * nodes * args.steps / t_e2e / 1e6, "unit": "MLUPS",
-           "h2d_bytes_per_step": (28 if mhd else 16) * nodes / args.steps,
+           "h2d_bytes_per_step": (8 if cg else (28 if mhd else 16)) * nodes / args.steps,
            "d2h_bytes_per_step": 16 * nodes / args.steps,
-           "note": "set_state from pinned host rho,u (16 B/node)" + (" and set_magnetic from pinned host b (12 B/node)"
-                                                                     if mhd else "") +
+           "note": ("set_colour_gradient from pinned host rho_r, rho_b (8 B/node)" if cg else
+                    "set_state from pinned host rho,u (16 B/node)" + (" and set_magnetic from pinned host b (12 B/node)"
+                                                                      if mhd else "")) +
                    " + K steps + macroscopic to pinned host (16 B/node); bytes per step are the job's totals / K"}
 
     if rank != 0:
@@ -466,7 +519,7 @@ def run_ours(args, wl):
     peak = peaks.get("hbm_gbs")
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
-    bpn = MHD_BYTES_PER_NODE if mhd else BYTES_PER_NODE[args.storage]
+    bpn = CG_BYTES_PER_NODE if cg else (MHD_BYTES_PER_NODE if mhd else BYTES_PER_NODE[args.storage])
     coll_avg_ms = prof["collide_ms"] / max(1, prof["collide_launches"])
     achieved = bpn * nodes / (coll_avg_ms * 1e-3) / 1e9
     traffic = committed_traffic(args.workload, args.storage)
@@ -487,10 +540,11 @@ def run_ours(args, wl):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["text"] + f", {args.storage} storage", "nodes": nodes, "storage": args.storage,
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU",
-                   "l2": f"inputs larger than L2: population store {27 * nodes * (4 if args.storage == 'fp32' else 2) / 1e6:.0f} MB"
+                   "l2": f"inputs larger than L2: population store {(54 if cg else 27) * nodes * (4 if args.storage == 'fp32' else 2) / 1e6:.0f} MB"
                          " > 129 MB, swept in full every step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "k_mhd_step" if mhd else "k_stream_collide",
+                     "traffic": traffic,
+                     "kernel": "k_cg_fields + k_cg_step" if cg else ("k_mhd_step" if mhd else "k_stream_collide"),
                      "algorithmic_bytes_per_launch": bpn * nodes, "avg_launch_ms": coll_avg_ms,
                      "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback 6.8 TB/s"},
         "kernel_ms_per_step": {"stream_collide": coll_avg_ms,
@@ -516,6 +570,9 @@ def main():
         if wl["kind"] == "droplet":
             wl["radius"] = wl["radius"] * args.n / wl["n"]
         wl["text"] = wl["text"].replace(f"{wl['n']}^3", f"{args.n}^3")
+        if wl["kind"] == "cg":
+            wl["text"] = wl["text"].replace(f"{wl['n']}x{4 * wl['n']}x{wl['n']} (W={wl['n']}",
+                                            f"{args.n}x{4 * args.n}x{args.n} (W={args.n}")
         wl["n"] = args.n
     if args.impl == "reference":
         run_reference(args, wl)

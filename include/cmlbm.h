@@ -142,6 +142,38 @@ LBM_API lbm_status lbm_set_magnetic_populations(lbm_ctx* ctx, const float* h);
 /* b and j = curl b at the current time (N floats each, host or device, NULL to skip); syncs. */
 LBM_API lbm_status lbm_magnetic(lbm_ctx* ctx, float* bx, float* by, float* bz, float* jx, float* jy, float* jz);
 
+/* Colour-gradient two-phase model (App. D): red and blue fluids with D3Q27 populations f^r, f^b;
+ * the total f = f^r + f^b takes the central-moment collision of Sec. II with the enhanced
+ * equilibrium of App. D (phi_i(alpha), the sixth-order Hermite terms, the density-gradient terms
+ * Phi_i), then the perturbation operator (interfacial tension, amplitude A) and the recolouring
+ * (parameter beta) split it again.  Per node: phi = (rho_r/rho_r0 - rho_b/rho_b0) /
+ * (rho_r/rho_r0 + rho_b/rho_b0); alpha_b = 8/27, alpha_r = 1 - (1 - alpha_b) rho_b0/rho_r0;
+ * 1/nu = (1+phi)/(2 nu_r) + (1-phi)/(2 nu_b), omega = 1/(3 nu + 1/2) on k4..k8; gradients by the
+ * isotropic central stencil (a neighbour behind a y wall takes the node's value); body force
+ * F = (rho - (rho_r0 + rho_b0)/2) g (Sec. III, Rayleigh-Taylor instability).  Readings: the
+ * perturbation uses (c_i . grad phi)^2 (it then conserves mass); recolouring uses rho phi_i(alpha)
+ * as f^eq(rho, 0).  Initial state at rest: f^k_i = rho_k phi_i(alpha(phi)) from rho_r, rho_b
+ * (N floats each, host or device).  Afterwards the context's store holds the red populations
+ * (full, not deviations) and lbm_set_state / lbm_set_populations / lbm_get_populations answer
+ * LBM_ERR_UNSUPPORTED; lbm_step, lbm_macroscopic (rho = rho_r + rho_b, u with F/2) and lbm_stats
+ * work on the total.  Needs FP32 storage, no mask, no z slab, no magnetic field, force NONE;
+ * rho_b0 / rho_r0 <= 27/19.  Adds 116 B per node. */
+typedef struct {
+    double rho_r0, rho_b0; /* densities of the pure red and blue fluids */
+    double nu_r, nu_b;     /* their kinematic viscosities */
+    double A;              /* perturbation amplitude (interfacial tension) */
+    double beta;           /* recolouring parameter, 0..1 */
+    double g[3];           /* gravity vector of the body force */
+} lbm_cg_params;
+LBM_API lbm_status lbm_set_colour_gradient(lbm_ctx* ctx, const lbm_cg_params* params, const float* rho_r,
+                                           const float* rho_b);
+/* Colour densities at the current time (N floats each, host or device, NULL to skip); syncs. */
+LBM_API lbm_status lbm_colour_densities(lbm_ctx* ctx, float* rho_r, float* rho_b);
+/* Red and blue populations at the current time, natural order, full populations (27 N floats
+ * each, host or device).  Set: only at even parity. */
+LBM_API lbm_status lbm_get_colour_populations(lbm_ctx* ctx, float* fr, float* fb);
+LBM_API lbm_status lbm_set_colour_populations(lbm_ctx* ctx, const float* fr, const float* fb);
+
 /* Sets f = f^eq(rho, u), the complete (sixth-order Hermite) equilibrium of Eq. eq:truncation,
  * on every fluid node (rest state on solid nodes).  Arrays: N floats each, host or device.
  * Resets the step counter to 0. */

@@ -44,6 +44,12 @@ class LbmDomain(ctypes.Structure):
     ]
 
 
+class LbmCgParams(ctypes.Structure):
+    _fields_ = [("rho_r0", ctypes.c_double), ("rho_b0", ctypes.c_double), ("nu_r", ctypes.c_double),
+                ("nu_b", ctypes.c_double), ("A", ctypes.c_double), ("beta", ctypes.c_double),
+                ("g", ctypes.c_double * 3)]
+
+
 class LbmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{status_name(status)}: {msg}")
@@ -82,6 +88,14 @@ def lib():
         L.lbm_set_magnetic_populations.restype = st
         L.lbm_magnetic.argtypes = [_P] + [_P] * 6
         L.lbm_magnetic.restype = st
+        L.lbm_set_colour_gradient.argtypes = [_P, ctypes.POINTER(LbmCgParams), _P, _P]
+        L.lbm_set_colour_gradient.restype = st
+        L.lbm_colour_densities.argtypes = [_P, _P, _P]
+        L.lbm_colour_densities.restype = st
+        L.lbm_get_colour_populations.argtypes = [_P, _P, _P]
+        L.lbm_get_colour_populations.restype = st
+        L.lbm_set_colour_populations.argtypes = [_P, _P, _P]
+        L.lbm_set_colour_populations.restype = st
         L.lbm_set_state.argtypes = [_P, _P, _P, _P, _P]
         L.lbm_set_state.restype = st
         L.lbm_set_populations.argtypes = [_P, _P]

@@ -47,7 +47,13 @@ struct lbm_ctx {
     float omega_m = 1;
     float bw[3] = {0, 0, 0};  // b at the y walls
 
-    float* macro = nullptr;  // 4N: rho, ux, uy, uz (10N with the magnetic field: + b, j)
+    // colour-gradient two-phase model (App. D), off unless lbm_set_colour_gradient was called; the
+    // store f then holds the red populations (full, not deviations)
+    float* cgb = nullptr;  // 27 N: blue populations
+    float* cgf = nullptr;  // 2 N: phi, rho
+    CgParams cg{};
+
+    float* macro = nullptr;  // 4N: rho, ux, uy, uz (10N with the magnetic field: + b, j; 6N two-phase: + rho_r, rho_b)
     float* uprev = nullptr;  // 3N
     bool have_uprev = false;
     double* partials = nullptr;
@@ -204,7 +210,8 @@ lbm_status sync_and_check(lbm_ctx* c) {
 }
 
 lbm_status ensure_macro(lbm_ctx* c) {
-    if (!c->macro) CK(c, cudaMalloc(&c->macro, sizeof(float) * (c->hm ? 10 : 4) * c->NL), "cudaMalloc(macroscopic)");
+    if (!c->macro)
+        CK(c, cudaMalloc(&c->macro, sizeof(float) * (c->hm ? 10 : (c->cgb ? 6 : 4)) * c->NL), "cudaMalloc(macroscopic)");
     return LBM_OK;
 }
 
@@ -225,6 +232,10 @@ lbm_status run_macro(lbm_ctx* c) {
     const long long NL = c->NL;
     if (c->hm) {
         CK(c, launch_mhd_fields(p, c->f, c->hm, c->omega_m, c->bw, c->parity, m, c->stream), "magnetic fields kernel");
+        return LBM_OK;
+    }
+    if (c->cgb) {
+        CK(c, launch_cg_macro(p, c->cg, c->f, c->cgb, c->parity, m, c->stream), "two-phase fields kernel");
         return LBM_OK;
     }
     CK(c, DISPATCH(c, launch_macroscopic, p, c->f, c->parity, kernel_force_kind(c), m, m + NL, m + 2 * NL, m + 3 * NL,
@@ -252,6 +263,19 @@ lbm_status do_steps(lbm_ctx* c, int nsteps, bool trace) {
     KParams p = make_params(c);
     const int fk = kernel_force_kind(c);
     lbm_status st;
+    if (c->cgb) {
+        if (trace) return fail(c, LBM_ERR_UNSUPPORTED, "free streaming of the two-phase model");
+        if (c->force_kind != LBM_FORCE_NONE)
+            return fail(c, LBM_ERR_UNSUPPORTED, "the two-phase model has its own body force (lbm_cg_params.g)");
+        for (int s = 0; s < nsteps; ++s) {
+            if ((st = profile_mark(c, 0))) return st;
+            CK(c, launch_cg_step(p, c->cg, c->f, c->cgb, c->cgf, c->parity, c->stream), "two-phase step kernels");
+            if ((st = profile_mark(c, 0))) return st;
+            c->parity ^= 1;
+            ++c->t;
+        }
+        return LBM_OK;
+    }
     if (c->hm) {
         if (trace) return fail(c, LBM_ERR_UNSUPPORTED, "free streaming with the magnetic field");
         if (c->force_kind != LBM_FORCE_NONE && c->force_kind != LBM_FORCE_UNIFORM)
@@ -285,6 +309,8 @@ void free_all(lbm_ctx* c) {
     c->events.clear();
     if (c->own_f && c->f) cudaFree(c->f);
     cudaFree(c->hm);
+    cudaFree(c->cgb);
+    cudaFree(c->cgf);
     cudaFree(c->links);
     cudaFree(c->kolm);
     cudaFree(c->field);
@@ -442,6 +468,7 @@ lbm_status lbm_set_magnetic(lbm_ctx* c, double eta, const double b_wall[3], cons
     if (!c) return LBM_ERR_ARG;
     if (c->storage != LBM_FP32) return fail(c, LBM_ERR_UNSUPPORTED, "the magnetic field needs FP32 storage");
     if (c->slab) return fail(c, LBM_ERR_UNSUPPORTED, "the magnetic field is not offered on z slabs");
+    if (c->cgb) return fail(c, LBM_ERR_UNSUPPORTED, "the magnetic field does not combine with the two-phase model");
     if (c->has_mask) return fail(c, LBM_ERR_UNSUPPORTED, "the magnetic field takes no solid mask");
     if (c->force_kind != LBM_FORCE_NONE && c->force_kind != LBM_FORCE_UNIFORM)
         return fail(c, LBM_ERR_UNSUPPORTED, "the magnetic field combines with no force or a uniform one only");
@@ -502,7 +529,93 @@ static lbm_status magnetic_copy(lbm_ctx* c, float* h, int to_buf) {
     return LBM_OK;
 }
 
+lbm_status lbm_set_colour_gradient(lbm_ctx* c, const lbm_cg_params* prm, const float* rho_r, const float* rho_b) {
+    if (!c) return LBM_ERR_ARG;
+    if (!prm || !rho_r || !rho_b) return fail(c, LBM_ERR_ARG, "params, rho_r and rho_b are required");
+    if (c->storage != LBM_FP32) return fail(c, LBM_ERR_UNSUPPORTED, "the two-phase model needs FP32 storage");
+    if (c->slab || c->has_mask) return fail(c, LBM_ERR_UNSUPPORTED, "the two-phase model takes no z slab or mask");
+    if (c->hm) return fail(c, LBM_ERR_UNSUPPORTED, "the two-phase model does not combine with the magnetic field");
+    if (c->force_kind != LBM_FORCE_NONE)
+        return fail(c, LBM_ERR_UNSUPPORTED, "the two-phase model has its own body force (lbm_cg_params.g)");
+    if (!(prm->rho_r0 > 0) || !(prm->rho_b0 > 0) || !(prm->nu_r > 0) || !(prm->nu_b > 0) || !(prm->A >= 0) ||
+        !(prm->beta >= 0 && prm->beta <= 1))
+        return fail(c, LBM_ERR_ARG, "rho_r0, rho_b0, nu_r, nu_b > 0, A >= 0, 0 <= beta <= 1");
+    if (prm->rho_b0 > prm->rho_r0 * 27.0 / 19.0)
+        return fail(c, LBM_ERR_ARG, "rho_b0 / rho_r0 <= 27/19 (alpha_r >= 0)");
+    c->cg.rho_r0 = prm->rho_r0;
+    c->cg.rho_b0 = prm->rho_b0;
+    c->cg.nu_r = prm->nu_r;
+    c->cg.nu_b = prm->nu_b;
+    c->cg.A = prm->A;
+    c->cg.beta = prm->beta;
+    for (int a = 0; a < 3; ++a) c->cg.g[a] = prm->g[a];
+    if (!c->cgb) {
+        CK(c, cudaMalloc(&c->cgb, sizeof(float) * 27 * c->N), "cudaMalloc(blue store)");
+        CK(c, cudaMalloc(&c->cgf, sizeof(float) * 2 * c->N), "cudaMalloc(phase fields)");
+        cudaFree(c->macro);  // the field buffer grows to 6 planes
+        c->macro = nullptr;
+    }
+    lbm_status st = ensure_macro(c);
+    if (st) return st;
+    float* rr = c->macro + 4 * c->NL;  // scratch: the colour-density planes of the field buffer
+    float* rb = c->macro + 5 * c->NL;
+    CK(c, copy_in(rr, rho_r, sizeof(float) * c->NL, c->stream), "red density copy");
+    CK(c, copy_in(rb, rho_b, sizeof(float) * c->NL, c->stream), "blue density copy");
+    KParams p = make_params(c);
+    CK(c, launch_cg_init(p, c->cg, c->f, c->cgb, rr, rb, c->stream), "two-phase init kernel");
+    CK(c, cudaStreamSynchronize(c->stream), "two-phase init sync");
+    c->t = 0;
+    c->parity = 0;
+    c->have_uprev = false;
+    return LBM_OK;
+}
+
+static lbm_status colour_copy(lbm_ctx* c, float* fr, float* fb, int to_buf) {
+    if (!c) return LBM_ERR_ARG;
+    if (!c->cgb) return fail(c, LBM_ERR_STATE, "no two-phase model: call lbm_set_colour_gradient first");
+    if (!fr || !fb) return fail(c, LBM_ERR_ARG, "fr and fb are required");
+    if (!to_buf && c->parity) return fail(c, LBM_ERR_STATE, "set colour populations after an even number of steps");
+    const size_t half = sizeof(float) * 27 * c->NL;
+    float* tmp = nullptr;
+    CK(c, cudaMalloc(&tmp, 2 * half), "cudaMalloc(staging)");
+    cudaError_t e = cudaSuccess;
+    if (!to_buf) {
+        e = copy_in(tmp, fr, half, c->stream);
+        if (e == cudaSuccess) e = copy_in(tmp + 27 * c->NL, fb, half, c->stream);
+    }
+    KParams p = make_params(c);
+    if (e == cudaSuccess) e = launch_cg_copy(p, c->cg, c->f, c->cgb, c->parity, tmp, to_buf, c->stream);
+    if (e == cudaSuccess && to_buf) {
+        e = copy_out(fr, tmp, half, c->stream);
+        if (e == cudaSuccess) e = copy_out(fb, tmp + 27 * c->NL, half, c->stream);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "colour populations");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "colour populations sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_colour_populations(lbm_ctx* c, float* fr, float* fb) { return colour_copy(c, fr, fb, 1); }
+
+lbm_status lbm_set_colour_populations(lbm_ctx* c, const float* fr, const float* fb) {
+    lbm_status st = colour_copy(c, const_cast<float*>(fr), const_cast<float*>(fb), 0);
+    if (st == LBM_OK) c->have_uprev = false;
+    return st;
+}
+
+lbm_status lbm_colour_densities(lbm_ctx* c, float* rho_r, float* rho_b) {
+    if (!c) return LBM_ERR_ARG;
+    if (!c->cgb) return fail(c, LBM_ERR_STATE, "no two-phase model: call lbm_set_colour_gradient first");
+    lbm_status st = run_macro(c);
+    if (st) return st;
+    if (rho_r) CK(c, copy_out(rho_r, c->macro + 4 * c->NL, sizeof(float) * c->NL, c->stream), "red density copy");
+    if (rho_b) CK(c, copy_out(rho_b, c->macro + 5 * c->NL, sizeof(float) * c->NL, c->stream), "blue density copy");
+    return sync_and_check(c);
+}
+
 lbm_status lbm_set_state(lbm_ctx* c, const float* rho, const float* ux, const float* uy, const float* uz) {
+    if (c && c->cgb) return fail(c, LBM_ERR_UNSUPPORTED, "two-phase model: lbm_set_colour_gradient sets the two-phase state");
     if (!c) return LBM_ERR_ARG;
     if (!rho || !ux || !uy || !uz) return fail(c, LBM_ERR_ARG, "rho, ux, uy, uz are required");
     lbm_status st = ensure_macro(c);
@@ -524,6 +637,7 @@ lbm_status lbm_set_state(lbm_ctx* c, const float* rho, const float* ux, const fl
 }
 
 lbm_status lbm_set_populations(lbm_ctx* c, const float* g) {
+    if (c && c->cgb) return fail(c, LBM_ERR_UNSUPPORTED, "two-phase model: use lbm_set_colour_populations");
     if (!c) return LBM_ERR_ARG;
     if (!g) return fail(c, LBM_ERR_ARG, "g is NULL");
     const float* src = g;
@@ -550,6 +664,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const float* g) {
 }
 
 lbm_status lbm_get_populations(lbm_ctx* c, float* g) {
+    if (c && c->cgb) return fail(c, LBM_ERR_UNSUPPORTED, "two-phase model: use lbm_get_colour_populations");
     if (!c) return LBM_ERR_ARG;
     if (!g) return fail(c, LBM_ERR_ARG, "g is NULL");
     float* dst = g;
@@ -708,7 +823,7 @@ struct CkptHeader {
 
 lbm_status lbm_save(lbm_ctx* c, const char* path) {
     if (!c || !path) return LBM_ERR_ARG;
-    if (c->hm) return fail(c, LBM_ERR_UNSUPPORTED, "checkpoint files hold the fluid store only");
+    if (c->hm || c->cgb) return fail(c, LBM_ERR_UNSUPPORTED, "checkpoint files hold the fluid store only");
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "CMLBMCK1", 8);
@@ -742,7 +857,7 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
 
 lbm_status lbm_load(lbm_ctx* c, const char* path) {
     if (!c || !path) return LBM_ERR_ARG;
-    if (c->hm) return fail(c, LBM_ERR_UNSUPPORTED, "checkpoint files hold the fluid store only");
+    if (c->hm || c->cgb) return fail(c, LBM_ERR_UNSUPPORTED, "checkpoint files hold the fluid store only");
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return fail(c, LBM_ERR_ARG, std::string("cannot open ") + path);
     CkptHeader h;

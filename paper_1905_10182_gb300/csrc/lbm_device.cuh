@@ -353,12 +353,19 @@ __device__ __forceinline__ void hermite2_correction(T (&K)[3][3][3], T rho, T ux
                        Fz * uz * (6.0f * X * Y + X + Y));
 }
 
+// No change of the equilibrium (the default of collide_increment's Extra hook).
+struct NoExtra {
+    __device__ __forceinline__ void operator()(float (&)[3][3][3], float, float, float, float, float) const {}
+};
+
 // In: K[x][y][z] holds the deviations g arranged by velocity (index c + 1).  Out: K holds the
 // increments dg arranged the same way.  Returns rho and u of the node.  HO: add the
-// second-order-truncation terms of hermite2_correction (weights ce, cf).
-template <bool HO = false>
+// second-order-truncation terms of hermite2_correction (weights ce, cf).  extra(K, rho, ux, uy,
+// uz, omega) may add further equilibrium terms to the increments before the inverse transform.
+template <bool HO = false, typename Extra = NoExtra>
 __device__ __forceinline__ Macro collide_increment(float (&K)[3][3][3], float Fx, float Fy, float Fz, float omega,
-                                                   float rho0, float ce = 0.0f, float cf = 0.0f) {
+                                                   float rho0, float ce = 0.0f, float cf = 0.0f,
+                                                   const Extra& extra = Extra()) {
     constexpr float s[3] = {1.0f, 0.0f, 1.0f / 3.0f};
 
     // raw moments of the deviations: z, then y, then x (index: [x][y][z], each either a velocity
@@ -436,6 +443,7 @@ __device__ __forceinline__ Macro collide_increment(float (&K)[3][3][3], float Fx
     K[2][2][1] = Fz * (1.0f / 18.0f) - K[2][2][1];
     K[2][2][2] = dr * (1.0f / 27.0f) - K[2][2][2];
     if (HO) hermite2_correction(K, rho, ux, uy, uz, Fx, Fy, Fz, ce, cf);
+    extra(K, rho, ux, uy, uz, omega);
 
     // step 4: dg = (T^T)^-1 dk, z then y then x inverses; g* = g + dg
     const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
@@ -457,13 +465,13 @@ __device__ __forceinline__ Macro collide_increment(float (&K)[3][3][3], float Fx
     return Macro{rho, ux, uy, uz};
 }
 
-template <bool HO = false>
+template <bool HO = false, typename Extra = NoExtra>
 __device__ __forceinline__ Macro collide_cm(float (&g)[27], float Fx, float Fy, float Fz, float omega, float rho0,
-                                            float ce = 0.0f, float cf = 0.0f) {
+                                            float ce = 0.0f, float cf = 0.0f, const Extra& extra = Extra()) {
     float K[3][3][3];
 #pragma unroll
     for (int i = 0; i < 27; ++i) K[dir_x(i) + 1][dir_y(i) + 1][dir_z(i) + 1] = g[i];
-    const Macro m = collide_increment<HO>(K, Fx, Fy, Fz, omega, rho0, ce, cf);
+    const Macro m = collide_increment<HO, Extra>(K, Fx, Fy, Fz, omega, rho0, ce, cf, extra);
 #pragma unroll
     for (int i = 0; i < 27; ++i) g[i] += K[dir_x(i) + 1][dir_y(i) + 1][dir_z(i) + 1];
     return m;

@@ -46,6 +46,20 @@ cudaError_t launch_mhd_init(const KParams& p, const void* f, float* hm, int odd,
 cudaError_t launch_mhd_copy(const KParams& p, float* hm, const float bw[3], int odd, float* buf, int to_buf,
                             cudaStream_t st);
 
+// lbm_cg.cu: the colour-gradient model of App. D; fr = the context's store (red, full populations),
+// fb the blue store, fld 2 N (phi, rho); macro out: 6 planes (rho, u, rho_r, rho_b)
+struct CgParams {
+    double rho_r0, rho_b0, nu_r, nu_b, A, beta, g[3];
+};
+cudaError_t launch_cg_step(const KParams& p, const CgParams& c, void* fr, float* fb, float* fld, int odd,
+                           cudaStream_t st);
+cudaError_t launch_cg_macro(const KParams& p, const CgParams& c, const void* fr, float* fb, int odd, float* out,
+                            cudaStream_t st);
+cudaError_t launch_cg_init(const KParams& p, const CgParams& c, void* fr, float* fb, const float* rr, const float* rb,
+                           cudaStream_t st);
+cudaError_t launch_cg_copy(const KParams& p, const CgParams& c, void* fr, float* fb, int odd, float* buf, int to_buf,
+                           cudaStream_t st);
+
 // lbm_reduce.cu: FP64 diagnostics over the macroscopic fields
 struct ReduceArgs {
     int nx, ny, nz;

@@ -30,7 +30,9 @@ class Solver:
     """One D3Q27 central-moment LBM domain on the current CUDA device."""
 
     def __init__(self, nx, ny, nz, nu, rho0=1.0, walls_y=False, mask=None, storage="fp32", stream=None,
-                 torch_store=True, slab_z=False):
+                 torch_store=True, slab_z=False, store=None):
+        """store: an optional caller-owned CUDA uint8 tensor of at least lbm_store_bytes bytes,
+        256-byte aligned, used as the population store (kept alive by the solver)."""
         self._lib = nat.lib()
         self.shape = (int(nz), int(ny), int(nx))
         self.N = int(nx) * int(ny) * int(nz)
@@ -58,7 +60,12 @@ class Solver:
                 nbytes = self._lib.lbm_store_bytes(ctypes.byref(d))
                 if nbytes == 0:
                     raise nat.LbmError(nat.LBM_ERR_ARG, "invalid grid")
-                self._store = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+                if store is not None:
+                    if store.numel() * store.element_size() < nbytes:
+                        raise nat.LbmError(nat.LBM_ERR_ARG, "store smaller than lbm_store_bytes")
+                    self._store = store
+                else:
+                    self._store = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
                 d.store = self._store.data_ptr()
         d.stream = int(stream) if stream else None
         self.desc = d
@@ -160,6 +167,28 @@ class Solver:
         out = [np.empty(self.shape, dtype=np.float32) for _ in range(6)]
         self._check(self._lib.lbm_magnetic(self._h, *(nat.ptr(a) for a in out)))
         return np.stack(out[:3]), np.stack(out[3:])
+
+    # -- colour-gradient two-phase model (App. D)
+    def set_colour_gradient(self, rho_r, rho_b, rho_r0, rho_b0, nu_r, nu_b, A=1e-4, beta=0.7, g=(0.0, 0.0, 0.0)):
+        """Turns on the red/blue model from the colour densities rho_r, rho_b (grid-shaped, at rest)."""
+        prm = nat.LbmCgParams(float(rho_r0), float(rho_b0), float(nu_r), float(nu_b), float(A), float(beta),
+                              (ctypes.c_double * 3)(*[float(v) for v in g]))
+        rr, rb = _f32(rho_r), _f32(rho_b)
+        self._check(self._lib.lbm_set_colour_gradient(self._h, ctypes.byref(prm), nat.ptr(rr), nat.ptr(rb)))
+
+    def colour_densities(self):
+        rr, rb = (np.empty(self.shape, dtype=np.float32) for _ in range(2))
+        self._check(self._lib.lbm_colour_densities(self._h, nat.ptr(rr), nat.ptr(rb)))
+        return rr, rb
+
+    def get_colour_populations(self):
+        fr, fb = (np.empty((27,) + self.shape, dtype=np.float32) for _ in range(2))
+        self._check(self._lib.lbm_get_colour_populations(self._h, nat.ptr(fr), nat.ptr(fb)))
+        return fr, fb
+
+    def set_colour_populations(self, fr, fb):
+        fr, fb = _f32(fr), _f32(fb)
+        self._check(self._lib.lbm_set_colour_populations(self._h, nat.ptr(fr), nat.ptr(fb)))
 
     def stats(self):
         out = (ctypes.c_double * nat.LBM_STATS_LEN)()
