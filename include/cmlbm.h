@@ -285,7 +285,8 @@ typedef struct {
 } lbm_domain;
 
 /* Creates the batch (all domains at rest: rho = rho0, u = 0) on the current device and stream.
- * Population memory: 108 B per node in one pool, plus 16 B per node (links, previous u). */
+ * Population memory: 108 B per node in one pool, plus 16 B per node (links, previous u).  Each
+ * domain holds fewer than 2^32 / 27 (159 M) nodes, else LBM_ERR_ARG. */
 LBM_API lbm_status lbm_batch_create(const lbm_domain* domains, int count, double rho0, void* stream, lbm_batch** out);
 
 /* Times trial_steps (rounded to even, >= 2) graph-replayed steps for each candidate launch shape

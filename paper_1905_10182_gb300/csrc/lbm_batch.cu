@@ -71,6 +71,35 @@ __device__ __forceinline__ void decode(uint32_t n, const BatchDomain& d, int& x,
 
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
+// AA gather / scatter of one domain (links always present) on 32-bit element offsets: a domain
+// holds fewer than 2^32 / 27 nodes, so the bounce-back choice between two slots is a select of two
+// 32-bit offsets followed by one address computation (the generic 64-bit form computes both
+// addresses).
+template <bool ODD>
+__device__ __forceinline__ void batch_gather(const float* __restrict__ f, uint32_t N, const Nbr& nb, uint32_t link,
+                                             float (&g)[27]) {
+    const uint32_t self = nb.self();
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        uint32_t off = (uint32_t)i * N + self;
+        if (ODD && !((link >> i) & 1u)) off = (uint32_t)dir_opp(i) * N + nb.at(-dir_x(i), -dir_y(i), -dir_z(i));
+        g[i] = f[off];
+    }
+}
+
+template <bool ODD>
+__device__ __forceinline__ void batch_scatter(float* __restrict__ f, uint32_t N, const Nbr& nb, uint32_t link,
+                                              const float (&g)[27]) {
+    const uint32_t self = nb.self();
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        uint32_t off = (uint32_t)dir_opp(i) * N + self;
+        // x + c_i is blocked exactly when the source of direction opp(i) is
+        if (ODD && !((link >> dir_opp(i)) & 1u)) off = (uint32_t)i * N + nb.at(dir_x(i), dir_y(i), dir_z(i));
+        f[off] = g[i];
+    }
+}
+
 // One AA step of every node of every active tile.  Blocks are persistent.  Schedules:
 //  0 strided: block b takes tiles b, b + grid, b + 2 grid, ...; the tiles in flight form one
 //    compact wavefront through the tile list, so an odd step finds the rows and planes its
@@ -103,7 +132,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_step(const BatchDomain* __rest
         decode(n, d, x, y, z);
         const Nbr nb = make_nbr(x, y, z, d);
         float g[27];
-        aa_gather<float, ODD, true>(f, (long long)d.N, nb, link, g);
+        batch_gather<ODD>(f, d.N, nb, link, g);
         if (SCHED != 0 && t + t_step < t_end) {
             const BatchTile nt = tiles[t + t_step];
             const uint32_t nn = nt.start + threadIdx.x;
@@ -119,7 +148,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_step(const BatchDomain* __rest
         const float u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
         const bool bad = !(m.rho > 0.0f) || !(u2 < 1.0f);
         if (__any_sync(__activemask(), bad) && bad) atomicOr(flag, 1u);
-        aa_scatter<float, ODD, true>(f, (long long)d.N, nb, link, g);
+        batch_scatter<ODD>(f, d.N, nb, link, g);
     }
 }
 
@@ -458,7 +487,7 @@ lbm_status lbm_batch_create(const lbm_domain* d, int count, double rho0, void* s
     for (int k = 0; k < count; ++k) {
         if (d[k].nx < 1 || d[k].ny < 1 || d[k].nz < 1 || !(d[k].nu > 0.0)) return bail(LBM_ERR_ARG);
         const long long N = (long long)d[k].nx * d[k].ny * d[k].nz;
-        if (N >= (1LL << 31)) return bail(LBM_ERR_ARG);
+        if (27 * N >= (1LL << 32)) return bail(LBM_ERR_ARG);  // 32-bit element offsets within a domain
         BatchDomain bd;
         std::memset(&bd, 0, sizeof(bd));
         bd.nx = d[k].nx;
