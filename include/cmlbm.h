@@ -130,7 +130,8 @@ LBM_API lbm_status lbm_set_hermite_orders(lbm_ctx* ctx, int eq_order, int force_
  * state; bx, by, bz: N floats each (host or device; NULL: zero).  Every later lbm_step advances
  * both; lbm_macroscopic and lbm_stats include j x b / 2 in u.  Needs FP32 storage, no solid mask,
  * no z slab, force NONE or UNIFORM, even parity (after lbm_set_state or an even number of
- * steps): else LBM_ERR_UNSUPPORTED / LBM_ERR_STATE.  eta > 0.  Adds 84 B per node. */
+ * steps), fewer than 2^32 / 27 (159 M) nodes: else LBM_ERR_UNSUPPORTED / LBM_ERR_STATE.  eta > 0.
+ * Adds 84 B per node. */
 LBM_API lbm_status lbm_set_magnetic(lbm_ctx* ctx, double eta, const double b_wall[3], const float* bx,
                                     const float* by, const float* bz);
 
@@ -156,8 +157,8 @@ LBM_API lbm_status lbm_magnetic(lbm_ctx* ctx, float* bx, float* by, float* bz, f
  * (N floats each, host or device).  Afterwards the context's store holds the red populations
  * (full, not deviations) and lbm_set_state / lbm_set_populations / lbm_get_populations answer
  * LBM_ERR_UNSUPPORTED; lbm_step, lbm_macroscopic (rho = rho_r + rho_b, u with F/2) and lbm_stats
- * work on the total.  Needs FP32 storage, no mask, no z slab, no magnetic field, force NONE;
- * rho_b0 / rho_r0 <= 27/19.  Adds 116 B per node. */
+ * work on the total.  Needs FP32 storage, no mask, no z slab, no magnetic field, force NONE,
+ * fewer than 2^32 / 27 (159 M) nodes; rho_b0 / rho_r0 <= 27/19.  Adds 116 B per node. */
 typedef struct {
     double rho_r0, rho_b0; /* densities of the pure red and blue fluids */
     double nu_r, nu_b;     /* their kinematic viscosities */

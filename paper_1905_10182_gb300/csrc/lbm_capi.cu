@@ -473,6 +473,7 @@ lbm_status lbm_set_magnetic(lbm_ctx* c, double eta, const double b_wall[3], cons
     if (c->force_kind != LBM_FORCE_NONE && c->force_kind != LBM_FORCE_UNIFORM)
         return fail(c, LBM_ERR_UNSUPPORTED, "the magnetic field combines with no force or a uniform one only");
     if (!(eta > 0.0)) return fail(c, LBM_ERR_ARG, "eta must be > 0");
+    if (27 * c->N >= (1LL << 32)) return fail(c, LBM_ERR_UNSUPPORTED, "the magnetic field needs fewer than 2^32/27 nodes");
     if (c->parity) return fail(c, LBM_ERR_STATE, "set the magnetic field after an even number of steps");
     const double om = 1.0 / (eta / 0.25 + 0.5);
     if (!(om < 2.0)) return fail(c, LBM_ERR_ARG, "eta too small for a stable omega_m");
@@ -540,6 +541,8 @@ lbm_status lbm_set_colour_gradient(lbm_ctx* c, const lbm_cg_params* prm, const f
     if (!(prm->rho_r0 > 0) || !(prm->rho_b0 > 0) || !(prm->nu_r > 0) || !(prm->nu_b > 0) || !(prm->A >= 0) ||
         !(prm->beta >= 0 && prm->beta <= 1))
         return fail(c, LBM_ERR_ARG, "rho_r0, rho_b0, nu_r, nu_b > 0, A >= 0, 0 <= beta <= 1");
+    if (27 * c->N >= (1LL << 32))
+        return fail(c, LBM_ERR_UNSUPPORTED, "the two-phase model needs fewer than 2^32/27 nodes");
     if (prm->rho_b0 > prm->rho_r0 * 27.0 / 19.0)
         return fail(c, LBM_ERR_ARG, "rho_b0 / rho_r0 <= 27/19 (alpha_r >= 0)");
     c->cg.rho_r0 = prm->rho_r0;

@@ -127,15 +127,11 @@ __device__ __forceinline__ void gather_two(const float* __restrict__ fr, const f
     const uint32_t self = nb.self();
     rr = 0.0f;
     rb = 0.0f;
+    const uint32_t NN = (uint32_t)N;  // 27 N < 2^32 (lbm_set_colour_gradient): 32-bit offsets
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
-        long long a;
-        if (!ODD) {
-            a = (long long)i * N + self;
-        } else {
-            const bool blocked = LINKS && ((link >> i) & 1u);
-            a = blocked ? (long long)i * N + self : (long long)dir_opp(i) * N + nb.at(-dir_x(i), -dir_y(i), -dir_z(i));
-        }
+        uint32_t a = (uint32_t)i * NN + self;
+        if (ODD && !(LINKS && ((link >> i) & 1u))) a = (uint32_t)dir_opp(i) * NN + nb.at(-dir_x(i), -dir_y(i), -dir_z(i));
         const float r = fr[a], b = fb[a];
         rr += r;
         rb += b;
@@ -210,13 +206,9 @@ __global__ void __launch_bounds__(CG_BLOCK, 3) k_cg_step(KParams p, CgArgs q, fl
         const float cosv = shell_of(i) == 0 ? 0.0f : cg * inv_gn * inv_len(i);
         const float r = fr_share * fs + rec * cosv * phi_w(i, alpha);
         // AA scatter of both colours
-        long long a;
-        if (!ODD) {
-            a = (long long)dir_opp(i) * p.N + self;
-        } else {
-            const bool blocked = LINKS && ((link >> dir_opp(i)) & 1u);
-            a = blocked ? (long long)dir_opp(i) * p.N + self : (long long)i * p.N + nb.at(dir_x(i), dir_y(i), dir_z(i));
-        }
+        const uint32_t NN = (uint32_t)p.N;
+        uint32_t a = (uint32_t)dir_opp(i) * NN + self;
+        if (ODD && !(LINKS && ((link >> dir_opp(i)) & 1u))) a = (uint32_t)i * NN + nb.at(dir_x(i), dir_y(i), dir_z(i));
         fr[a] = r;
         q.fb[a] = fs - r;
     }

@@ -114,10 +114,24 @@ struct Nbr {
 // source is blocked, in slot i of x: halfway bounce-back); f*_i goes to slot i of x + c_i (or,
 // when x + c_i is blocked, to slot opp(i) of x).  Each node reads and writes the same 27
 // slots, so the update is race free in place and leaves natural order after every odd step.
-template <typename S, bool ODD, bool LINKS>
+// OFF32: element offsets in 32 bits (the caller guarantees 27 N < 2^32): the bounce-back choice
+// is a select of two 32-bit offsets and one address computation, which saves instructions and
+// registers over the general 64-bit form.
+template <typename S, bool ODD, bool LINKS, bool OFF32 = false>
 __device__ __forceinline__ void aa_gather(const S* __restrict__ f, long long N, const Nbr& nb, uint32_t link,
                                           float (&g)[27]) {
     const uint32_t self = nb.self();
+    if (OFF32) {
+        const uint32_t NN = (uint32_t)N;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            uint32_t off = (uint32_t)i * NN + self;
+            if (ODD && !(LINKS && ((link >> i) & 1u)))
+                off = (uint32_t)dir_opp(i) * NN + nb.at(-dir_x(i), -dir_y(i), -dir_z(i));
+            g[i] = Codec<S>::ld(f + off);
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         const S* p;
@@ -132,10 +146,22 @@ __device__ __forceinline__ void aa_gather(const S* __restrict__ f, long long N, 
     }
 }
 
-template <typename S, bool ODD, bool LINKS>
+template <typename S, bool ODD, bool LINKS, bool OFF32 = false>
 __device__ __forceinline__ void aa_scatter(S* __restrict__ f, long long N, const Nbr& nb, uint32_t link,
                                            const float (&g)[27]) {
     const uint32_t self = nb.self();
+    if (OFF32) {
+        const uint32_t NN = (uint32_t)N;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            // x + c_i is blocked exactly when the source of direction opp(i) is
+            uint32_t off = (uint32_t)dir_opp(i) * NN + self;
+            if (ODD && !(LINKS && ((link >> dir_opp(i)) & 1u)))
+                off = (uint32_t)i * NN + nb.at(dir_x(i), dir_y(i), dir_z(i));
+            Codec<S>::st(f + off, g[i]);
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         S* p;

@@ -12,7 +12,8 @@
 //
 // Storage: h in FP32, h[(3 l + a) N + n], one array updated in place with the AA pattern of the
 // fluid store (same parity): even steps read and write a node's own slots (reversed), odd steps
-// read the neighbours' opposite slots and write the neighbours' slots.
+// read the neighbours' opposite slots and write the neighbours' slots.  A context with a magnetic
+// field holds fewer than 2^32 / 27 nodes, so element offsets are 32-bit.
 #include "lbm_device.cuh"
 #include "lbm_launch.h"
 
@@ -37,12 +38,13 @@ __device__ __forceinline__ void mhd_gather(const float* __restrict__ hm, long lo
         const uint32_t src = ODD ? nb.at(-dir_x(l), -dir_y(l), -dir_z(l)) : self;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
+            const uint32_t NN = (uint32_t)N;  // 27 N < 2^32 (lbm_set_magnetic)
             if (!ODD)
-                h[3 * l + a] = hm[(long long)(3 * l + a) * N + self];
+                h[3 * l + a] = hm[(uint32_t)(3 * l + a) * NN + self];
             else if (blocked)
-                h[3 * l + a] = -hm[(long long)(3 * l + a) * N + self] + 2.0f * wm(l) * bw[a];
+                h[3 * l + a] = -hm[(uint32_t)(3 * l + a) * NN + self] + 2.0f * wm(l) * bw[a];
             else
-                h[3 * l + a] = hm[(long long)(3 * opp7(l) + a) * N + src];
+                h[3 * l + a] = hm[(uint32_t)(3 * opp7(l) + a) * NN + src];
         }
     }
 }
@@ -59,12 +61,13 @@ __device__ __forceinline__ void mhd_scatter(float* __restrict__ hm, long long N,
         const uint32_t dst = ODD ? nb.at(dir_x(l), dir_y(l), dir_z(l)) : self;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
+            const uint32_t NN = (uint32_t)N;
             if (!ODD)
-                hm[(long long)(3 * opp7(l) + a) * N + self] = h[3 * l + a];
+                hm[(uint32_t)(3 * opp7(l) + a) * NN + self] = h[3 * l + a];
             else if (blocked)
-                hm[(long long)(3 * opp7(l) + a) * N + self] = -h[3 * l + a] + 2.0f * wm(l) * bw[a];
+                hm[(uint32_t)(3 * opp7(l) + a) * NN + self] = -h[3 * l + a] + 2.0f * wm(l) * bw[a];
             else
-                hm[(long long)(3 * l + a) * N + dst] = h[3 * l + a];
+                hm[(uint32_t)(3 * l + a) * NN + dst] = h[3 * l + a];
         }
     }
 }
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(MHD_BLOCK, 4) k_mhd_step(KParams p, MhdArgs q,
     float h[21];
     mhd_gather<ODD, LINKS>(q.hm, p.N, nb, link, q.bw, h);
     float g[27];
-    aa_gather<float, ODD, LINKS>(f, p.N, nb, link, g);
+    aa_gather<float, ODD, LINKS, true>(f, p.N, nb, link, g);
     const float Fe[3] = {p.F[0], p.F[1], p.F[2]};
     const MhdNode m = mhd_node(g, h, p.rho0, Fe, q.omega_m);
     mhd_collide(h, m.b, m.u, q.omega_m);
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(MHD_BLOCK, 4) k_mhd_step(KParams p, MhdArgs q,
     const float u2 = mc.ux * mc.ux + mc.uy * mc.uy + mc.uz * mc.uz;
     const bool bad = !(mc.rho > 0.0f) || !(u2 < 1.0f);
     if (__any_sync(__activemask(), bad) && bad) atomicOr(p.flag, 1u);
-    aa_scatter<float, ODD, LINKS>(f, p.N, nb, link, g);
+    aa_scatter<float, ODD, LINKS, true>(f, p.N, nb, link, g);
 }
 
 // rho, u (with (F_ext + F_L)/2), b, j at the current time; out: 10 planes of N (rho, u, b, j).
