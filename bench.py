@@ -522,7 +522,7 @@ def run_ours(args, wl):
     bpn = CG_BYTES_PER_NODE if cg else (MHD_BYTES_PER_NODE if mhd else BYTES_PER_NODE[args.storage])
     coll_avg_ms = prof["collide_ms"] / max(1, prof["collide_launches"])
     achieved = bpn * nodes / (coll_avg_ms * 1e-3) / 1e9
-    traffic = committed_traffic(args.workload, args.storage)
+    traffic = committed_traffic(args.workload, args.storage) if args.n in (None, WORKLOADS[args.workload]["n"]) else None
     # every kernel launched in the timed region: one stream-collide per step, plus psi (Shan-Chen)
     launches = args.steps * (2 if prof["psi_launches"] else 1)
 

@@ -22,25 +22,6 @@ using namespace cmlbm;
 
 namespace {
 
-// Division by a fixed divisor d >= 1 for dividends n < 2^31 without an integer divide:
-// q = umulhi(n, m) >> s, m = ceil(2^(31 + l) / d), s = l - 1, l = ceil(log2 d); exact because
-// m d - 2^(31 + l) < 2^l.  d = 1 passes n through.
-struct FastDiv {
-    uint32_t d, m, s;
-    __device__ __forceinline__ uint32_t div(uint32_t n) const { return d == 1 ? n : (__umulhi(n, m) >> s); }
-};
-
-FastDiv make_fastdiv(uint32_t d) {
-    FastDiv q{d, 0, 0};
-    if (d <= 1) return q;
-    uint32_t l = 0;
-    while ((1ull << l) < d) ++l;
-    const unsigned __int128 num = (unsigned __int128)1 << (31 + l);
-    q.m = (uint32_t)((num + d - 1) / d);
-    q.s = l - 1;
-    return q;
-}
-
 struct BatchDomain {
     uint32_t nx, ny, nz, N;
     unsigned long long f_off;     // first population element of the domain in the pool

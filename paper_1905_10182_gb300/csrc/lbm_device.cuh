@@ -41,6 +41,26 @@ __host__ __device__ constexpr float weight(int i) { return w1(dir_x(i)) * w1(dir
 
 constexpr uint32_t SOLID_BIT = 1u << 31;  // in a link word: the node itself is solid
 
+// Division by a fixed divisor d >= 1 for dividends n < 2^31 without an integer divide:
+// q = umulhi(n, m) >> s, m = ceil(2^(31 + l) / d), s = l - 1, l = ceil(log2 d); exact because
+// m d - 2^(31 + l) < 2^l.  d = 1 passes n through.
+struct FastDiv {
+    uint32_t d, m, s;
+    __device__ __forceinline__ uint32_t div(uint32_t n) const { return d == 1 ? n : (__umulhi(n, m) >> s); }
+    __device__ __forceinline__ uint32_t mod(uint32_t n) const { return n - div(n) * d; }
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv q{d, 0, 0};
+    if (d <= 1) return q;
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    const unsigned __int128 num = (unsigned __int128)1 << (31 + l);
+    q.m = (uint32_t)((num + d - 1) / d);
+    q.s = l - 1;
+    return q;
+}
+
 // ----------------------------------------------------------------------------- codecs
 template <typename S>
 struct Codec;

@@ -219,22 +219,30 @@ struct PairMap {
     uint32_t pair, y, z;
     bool owner, live;  // live: the warp maps to a row of the grid
 };
+// Divisors of the halo mapping, computed at launch: warps per row, pairs per row, rows per plane.
+struct PairDims {
+    FastDiv wpr, np, ny;
+};
+inline PairDims make_pair_dims(const KParams& p) {
+    const uint32_t np = (uint32_t)p.nx / 2;
+    return PairDims{make_fastdiv((np + 29u) / 30u), make_fastdiv(np), make_fastdiv((uint32_t)p.ny)};
+}
 template <bool HALO>
-__device__ __forceinline__ PairMap map_pair(const KParams& p) {
+__device__ __forceinline__ PairMap map_pair(const KParams& p, const PairDims& pd) {
     PairMap m;
     const uint32_t np = (uint32_t)p.nx / 2;
     if (HALO) {
         const uint32_t lane = threadIdx.x & 31u;
-        const uint32_t wpr = (np + 29u) / 30u;
         const uint32_t W = blockIdx.x * (X2_BLOCK / 32) + (threadIdx.x >> 5);
-        const uint32_t row = W / wpr;
+        const uint32_t row = pd.wpr.div(W);
         const uint32_t rows = (uint32_t)p.ny * (uint32_t)(p.nz - 2 * p.z0);
         m.live = row < rows;
-        const uint32_t qq = (W - row * wpr) * 30u + lane;  // pair + 1 within the row
+        const uint32_t qq = (W - row * pd.wpr.d) * 30u + lane;  // pair + 1 within the row
         m.owner = m.live && lane >= 1 && lane <= 30 && qq - 1 < np;
-        m.pair = qq == 0 ? np - 1 : (qq - 1) % np;
-        m.y = row % (uint32_t)p.ny;
-        m.z = row / (uint32_t)p.ny + (uint32_t)p.z0;
+        m.pair = qq == 0 ? np - 1 : pd.np.mod(qq - 1);
+        const uint32_t zr = pd.ny.div(row);
+        m.y = row - zr * (uint32_t)p.ny;
+        m.z = zr + (uint32_t)p.z0;
     } else {
         m.pair = blockIdx.x * X2_BLOCK + threadIdx.x;
         m.owner = m.pair < np;
@@ -258,14 +266,14 @@ inline dim3 x2_grid(const KParams& p) {
     return dim3((np + X2_BLOCK - 1) / X2_BLOCK, p.ny, rows_z);
 }
 
-// Element k * N + off of the store (plane k, node off; N < 2^31): one 32 x 32 -> 64-bit product.
-template <typename S>
-__device__ __forceinline__ uint32_t ld_word(const S* f, uint32_t N, uint32_t k, uint32_t off) {
-    return *reinterpret_cast<const uint32_t*>(f + ((uint64_t)N * k + off));
+// The 32-bit word of plane k at a row pointer: row + k * PB, PB = N * sizeof(S) bytes per plane.
+// Row pointers (one per (y, z) offset of the node pair, 64-bit) are formed once per thread, so
+// each access costs one 64-bit add of a constant plane offset.
+__device__ __forceinline__ uint32_t ld_word(const char* row, uint64_t PB, int k) {
+    return *reinterpret_cast<const uint32_t*>(row + PB * k);
 }
-template <typename S>
-__device__ __forceinline__ void st_word(S* f, uint32_t N, uint32_t k, uint32_t off, uint32_t w) {
-    *reinterpret_cast<uint32_t*>(f + ((uint64_t)N * k + off)) = w;
+__device__ __forceinline__ void st_word(char* row, uint64_t PB, int k, uint32_t w) {
+    *reinterpret_cast<uint32_t*>(row + PB * k) = w;
 }
 
 // Shan-Chen force on the pair (halo mapping): F = -G psi(x) sum_i w_i c_i psi(x + c_i)
@@ -301,11 +309,12 @@ __device__ __forceinline__ void shan_chen_x2(const KParams& p, const uint32_t (&
 }
 
 template <typename S, bool ODD, int FK, bool HO>
-__global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5)) k_stream_collide_x2(KParams p, S* __restrict__ f) {
+__global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5))
+    k_stream_collide_x2(KParams p, PairDims pd, S* __restrict__ f) {
     constexpr bool HALO = ODD || FK == FK_SHAN_CHEN;
     const unsigned full = 0xffffffffu;
     const uint32_t nx = p.nx, ny = p.ny, nz = p.nz;
-    const PairMap pm = map_pair<HALO>(p);
+    const PairMap pm = map_pair<HALO>(p, pd);
     if (!pm.live) return;  // a whole warp past the last row
     const bool owner = pm.owner;
     const uint32_t x0 = 2 * pm.pair;
@@ -316,7 +325,12 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5)) k_stream_collide_x2(K
     const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
     const uint32_t zo[3] = {zm * pl, z * pl, zp * pl};
     const uint32_t self = zo[1] + yo[1] + x0;
-    const uint32_t N = (uint32_t)p.N;
+    const uint64_t PB = (uint64_t)p.N * sizeof(S);
+    char* row[3][3];  // row[a][b]: the pair's word of plane 0 in row (y + b - 1, z + a - 1)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) row[a][b] = reinterpret_cast<char*>(f) + (uint64_t)(zo[a] + yo[b] + x0) * sizeof(S);
 
     // AA gather
     V2 g[27];
@@ -324,11 +338,11 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5)) k_stream_collide_x2(K
     for (int i = 0; i < 27; ++i) {
         uint32_t w;
         if (!ODD) {
-            w = ld_word(f, N, i, self);
+            w = ld_word(row[1][1], PB, i);
         } else {
             // f_i(x) sits in slot opp(i) of x - c_i
             const int dx = -dir_x(i);
-            const uint32_t own = ld_word(f, N, dir_opp(i), zo[1 - dir_z(i)] + yo[1 - dir_y(i)] + x0);
+            const uint32_t own = ld_word(row[1 - dir_z(i)][1 - dir_y(i)], PB, dir_opp(i));
             if (dx == 0) {
                 w = own;
             } else if (dx < 0) {  // sources x0 - 1 (left lane's high half), x0
@@ -369,11 +383,10 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5)) k_stream_collide_x2(K
     for (int i = 0; i < 27; ++i) {
         const uint32_t w = Pair<S>::pack(g[i]);
         if (!ODD) {
-            if (owner) st_word(f, N, dir_opp(i), self, w);
+            if (owner) st_word(row[1][1], PB, dir_opp(i), w);
         } else {
             // f*_i goes to slot i of x + c_i
             const int dx = dir_x(i);
-            const uint32_t a = zo[1 + dir_z(i)] + yo[1 + dir_y(i)] + x0;
             uint32_t v;
             if (dx == 0)
                 v = w;
@@ -381,7 +394,7 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5)) k_stream_collide_x2(K
                 v = __byte_perm(__shfl_up_sync(full, w, 1), w, 0x5432);
             else  // the pair at x0 receives (own node 1, right lane's node 0)
                 v = __byte_perm(w, __shfl_down_sync(full, w, 1), 0x5432);
-            if (owner) st_word(f, N, i, a, v);
+            if (owner) st_word(row[1 + dir_z(i)][1 + dir_y(i)], PB, i, v);
         }
     }
 }

@@ -112,7 +112,7 @@ def test_taylor_green_energy_decay_rate():
 
 
 def test_taylor_green_low_viscosity_curves_match_oracle(orc):
-    """64^3, U0 = 0.05, nu = 1e-4: the vortex goes through its transition (enstrophy grows fivefold,
+    """64^3, U0 = 0.05, nu = 1e-4: the vortex goes through its transition (enstrophy grows sixfold,
     then decays) within 5000 steps. Both curves, sampled every 250 steps, stay within 1e-4 relative
     of the FP64 oracle's (measured 2.3e-6 for the energy and 5.9e-6 for the enstrophy): the FP32
     rounding differences are amplified by the flow's instability, while a wrong term (a viscosity
