@@ -166,9 +166,9 @@ template <typename S, bool ODD, bool LINKS, bool HO>
 static cudaError_t launch_step_t(const KParams& p, S* f, int fk, bool trace, cudaStream_t st) {
     const dim3 grid = node_grid(p), block(BLOCK_X);
     if constexpr (sizeof(S) == 2 && !LINKS) {
-        // 16-bit storage, fully periodic, even nx, 4-byte aligned store: two nodes per thread
-        if (!trace && p.nx % 2 == 0 && (reinterpret_cast<uintptr_t>(f) & 3) == 0) {
-            const dim3 grid2 = x2_grid<ODD>(p), grid_sc = x2_grid<true>(p);
+        // 16-bit storage, fully periodic, nx a multiple of 64, 4-byte aligned store: two nodes per thread
+        if (!trace && p.nx % 64 == 0 && (reinterpret_cast<uintptr_t>(f) & 3) == 0) {
+            const dim3 grid2 = x2_grid(p);
             const PairDims pd = make_pair_dims(p);
             switch (fk) {
             case FK_CONST: k_stream_collide_x2<S, ODD, FK_CONST, HO><<<grid2, X2_BLOCK, 0, st>>>(p, pd, f); break;
@@ -177,7 +177,7 @@ static cudaError_t launch_step_t(const KParams& p, S* f, int fk, bool trace, cud
                 break;
             case FK_FIELD: k_stream_collide_x2<S, ODD, FK_FIELD, HO><<<grid2, X2_BLOCK, 0, st>>>(p, pd, f); break;
             case FK_SHAN_CHEN:
-                k_stream_collide_x2<S, ODD, FK_SHAN_CHEN, HO><<<grid_sc, X2_BLOCK, 0, st>>>(p, pd, f);
+                k_stream_collide_x2<S, ODD, FK_SHAN_CHEN, HO><<<grid2, X2_BLOCK, 0, st>>>(p, pd, f);
                 break;
             default: return cudaErrorInvalidValue;
             }

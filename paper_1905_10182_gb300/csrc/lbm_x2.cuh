@@ -206,89 +206,114 @@ __device__ __forceinline__ Macro2 collide_direct_x2(V2 (&g)[27], V2 Fx, V2 Fy, V
 }
 
 // ----------------------------------------------------------------------------- the kernel
-// Thread -> node pair (x0 = 2 pair, x0 + 1) of a row (y, z).
-// HALO (odd steps and the Shan-Chen stencil, which need the x neighbours): warps are numbered over
-// all rows, wpr = ceil(np / 30) warps per row of np pairs; warp k of a row owns its pairs
-// 30k .. 30k + 29, and its lanes 0 and 31 take the pairs on either side (owned by the neighbouring
-// warps, wrapped periodically), so that every x neighbour of an owned pair is in the adjacent lane
-// and comes by a shuffle.  A halo lane computes only what its neighbour lane needs from it (node 1
-// of lane 0, node 0 of lane 31 are exact; the other node is not used) and stores nothing; lanes
-// past the row end take a wrapped pair and store nothing.  Warps past the last row return whole.
-// Otherwise (even steps without stencil) every lane of a block row segment owns one pair.
+// Thread -> node pair (x0 = 2 pair, x0 + 1) of a row (y, z): the pairs of all rows are numbered
+// row by row and thread G of the grid owns pair G.  The kernel is used for nx a multiple of 64, so
+// that every warp holds 32 pairs of one row: lane 0 and lane 31 are the only lanes whose x
+// neighbour pair (on the left, on the right; periodic in the row) is in another warp.
+//
+// The x neighbours (odd steps; the psi stencil of Shan-Chen) come from the adjacent lane by a warp
+// shuffle.  At the two edges of a warp the half-words are read and written directly, and only by
+// the warp whose nodes they belong to in the AA pattern: the 18 half-words that lanes 0 and 31
+// gather from outside the warp are loaded by lanes 0..17 in one instruction and passed on by
+// shuffles, and the half-words that lanes 0 and 31 scatter outside their own 32-bit words are
+// stored with 16-bit stores.  Every population slot is thus read and written only by the warp
+// that owns its node (no thread recomputes a node of another warp, whose slots that warp
+// overwrites), so the in-place update is race free in any order of the warps.
 struct PairMap {
     uint32_t pair, y, z;
-    bool owner, live;  // live: the warp maps to a row of the grid
 };
-// Divisors of the halo mapping, computed at launch: warps per row, pairs per row, rows per plane.
+// Launch-time divisors (pairs per row, rows per plane) and the number of pairs.
 struct PairDims {
-    FastDiv wpr, np, ny;
+    FastDiv np, ny;
+    uint32_t pairs;
 };
 inline PairDims make_pair_dims(const KParams& p) {
     const uint32_t np = (uint32_t)p.nx / 2;
-    return PairDims{make_fastdiv((np + 29u) / 30u), make_fastdiv(np), make_fastdiv((uint32_t)p.ny)};
+    return PairDims{make_fastdiv(np), make_fastdiv((uint32_t)p.ny), np * (uint32_t)p.ny * (uint32_t)(p.nz - 2 * p.z0)};
 }
-template <bool HALO>
-__device__ __forceinline__ PairMap map_pair(const KParams& p, const PairDims& pd) {
+__device__ __forceinline__ PairMap map_pair(const KParams& p, const PairDims& pd, uint32_t G) {
     PairMap m;
-    const uint32_t np = (uint32_t)p.nx / 2;
-    if (HALO) {
-        const uint32_t lane = threadIdx.x & 31u;
-        const uint32_t W = blockIdx.x * (X2_BLOCK / 32) + (threadIdx.x >> 5);
-        const uint32_t row = pd.wpr.div(W);
-        const uint32_t rows = (uint32_t)p.ny * (uint32_t)(p.nz - 2 * p.z0);
-        m.live = row < rows;
-        const uint32_t qq = (W - row * pd.wpr.d) * 30u + lane;  // pair + 1 within the row
-        m.owner = m.live && lane >= 1 && lane <= 30 && qq - 1 < np;
-        m.pair = qq == 0 ? np - 1 : pd.np.mod(qq - 1);
-        const uint32_t zr = pd.ny.div(row);
-        m.y = row - zr * (uint32_t)p.ny;
-        m.z = zr + (uint32_t)p.z0;
-    } else {
-        m.pair = blockIdx.x * X2_BLOCK + threadIdx.x;
-        m.owner = m.pair < np;
-        m.live = true;
-        if (!m.owner) m.pair = np - 1;
-        m.y = blockIdx.y;
-        m.z = blockIdx.z + (uint32_t)p.z0;
-    }
+    const uint32_t row = pd.np.div(G);
+    m.pair = G - row * pd.np.d;
+    const uint32_t zr = pd.ny.div(row);
+    m.y = row - zr * (uint32_t)p.ny;
+    m.z = zr + (uint32_t)p.z0;
     return m;
 }
 
 // launch grid of the pair kernel
-template <bool HALO>
 inline dim3 x2_grid(const KParams& p) {
-    const uint32_t np = (uint32_t)p.nx / 2;
-    const uint32_t rows_z = (uint32_t)(p.nz - 2 * p.z0);
-    if (HALO) {
-        const unsigned long long warps = (unsigned long long)((np + 29u) / 30u) * p.ny * rows_z;
-        return dim3((unsigned)((warps + X2_BLOCK / 32 - 1) / (X2_BLOCK / 32)), 1, 1);
+    return dim3((make_pair_dims(p).pairs + X2_BLOCK - 1) / X2_BLOCK, 1, 1);
+}
+
+// Edge loads of the gather: lane j < 9 loads for lane 0 the half-word of the j-th direction with
+// c_x = +1 (source x0 - 1), lane 9 + j for lane 31 that of the j-th direction with c_x = -1
+// (source x0 + 2).  edge_dir(j): that direction; edge_rank(i): the position of direction i among
+// the directions with its c_x.
+__host__ __device__ constexpr int edge_rank(int i) {
+    int n = 0;
+    for (int k = 0; k < i; ++k)
+        if (dir_x(k) == dir_x(i)) ++n;
+    return n;
+}
+__host__ __device__ constexpr int edge_dir(int j) {
+    const int cx = j < 9 ? 1 : -1, r = j < 9 ? j : j - 9;
+    for (int i = 0; i < 27; ++i)
+        if (dir_x(i) == cx && edge_rank(i) == r) return i;
+    return 0;
+}
+// six lanes per word, 9 bits each: the slot opp(d) (5 bits), dy + 1, dz + 1 (2 bits each) of d = edge_dir(j)
+__host__ __device__ constexpr unsigned long long pack_edges(int part) {
+    unsigned long long c = 0;
+    for (int e = 0; e < 6; ++e) {
+        const int d = edge_dir(6 * part + e);
+        c |= (unsigned long long)(dir_opp(d) | (dir_y(d) + 1) << 5 | (dir_z(d) + 1) << 7) << (9 * e);
     }
-    return dim3((np + X2_BLOCK - 1) / X2_BLOCK, p.ny, rows_z);
+    return c;
 }
 
 // The 32-bit word of plane k at a row pointer: row + k * PB, PB = N * sizeof(S) bytes per plane.
 // Row pointers (one per (y, z) offset of the node pair, 64-bit) are formed once per thread, so
 // each access costs one 64-bit add of a constant plane offset.
-__device__ __forceinline__ uint32_t ld_word(const char* row, uint64_t PB, int k) {
-    return *reinterpret_cast<const uint32_t*>(row + PB * k);
+__device__ __forceinline__ uint32_t ld_word(const char* a) { return *reinterpret_cast<const uint32_t*>(a); }
+__device__ __forceinline__ void st_word(char* a, uint32_t w) { *reinterpret_cast<uint32_t*>(a) = w; }
+// one 16-bit storage value (an edge half-word)
+__device__ __forceinline__ uint32_t ld_half(const char* a) { return *reinterpret_cast<const unsigned short*>(a); }
+// stores under a per-lane predicate, written as predicated instructions (no branch around them)
+__device__ __forceinline__ void st_word_if(char* a, uint32_t w, bool q) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p st.global.b32 [%0], %1;\n\t}" ::"l"(a), "r"(w),
+                 "r"((uint32_t)q)
+                 : "memory");
 }
-__device__ __forceinline__ void st_word(char* row, uint64_t PB, int k, uint32_t w) {
-    *reinterpret_cast<uint32_t*>(row + PB * k) = w;
+__device__ __forceinline__ void st_half_if(char* a, uint32_t h, bool q) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p st.global.b16 [%0], %1;\n\t}" ::"l"(a),
+                 "h"((unsigned short)h), "r"((uint32_t)q)
+                 : "memory");
+}
+// the value unchanged, opaque to the compiler (keeps it from holding values derived from it)
+__device__ __forceinline__ uint32_t opaque(uint32_t v) {
+    asm volatile("mov.b32 %0, %0;" : "+r"(v));
+    return v;
 }
 
-// Shan-Chen force on the pair (halo mapping): F = -G psi(x) sum_i w_i c_i psi(x + c_i)
-// (Sec. III, static droplet).
+// Shan-Chen force on the pair: F = -G psi(x) sum_i w_i c_i psi(x + c_i) (Sec. III, static
+// droplet); psi(x0 - 1) and psi(x0 + 2) by shuffle, loaded by lanes 0 and 31 (psi is read only).
 __device__ __forceinline__ void shan_chen_x2(const KParams& p, const uint32_t (&yo)[3], const uint32_t (&zo)[3],
-                                             uint32_t x0, V2& Fx, V2& Fy, V2& Fz) {
+                                             uint32_t x0, uint32_t lane, uint32_t xe, V2& Fx, V2& Fy, V2& Fz) {
     const unsigned full = 0xffffffffu;
     V2 sx = bc(0.0f), sy = bc(0.0f), sz = bc(0.0f), self = bc(0.0f);
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
-            const float2 c = *reinterpret_cast<const float2*>(p.psi + zo[dz + 1] + yo[dy + 1] + x0);
-            const float left = __shfl_up_sync(full, c.y, 1);    // psi(x0 - 1)
-            const float right = __shfl_down_sync(full, c.x, 1);  // psi(x0 + 2)
+            const float* r = p.psi + zo[dz + 1] + yo[dy + 1];
+            const float2 c = *reinterpret_cast<const float2*>(r + x0);
+            float e = 0.0f;
+            if (lane == 0 || lane == 31) e = r[xe];
+            float left = __shfl_up_sync(full, c.y, 1);    // psi(x0 - 1)
+            float right = __shfl_down_sync(full, c.x, 1);  // psi(x0 + 2)
+            if (lane == 0) left = e;
+            if (lane == 31) right = e;
             const V2 m = V2{make_float2(left, c.x)};    // psi(x - 1) of the pair
             const V2 z0 = V2{c};                        // psi(x)
             const V2 pl = V2{make_float2(c.y, right)};  // psi(x + 1)
@@ -311,12 +336,12 @@ __device__ __forceinline__ void shan_chen_x2(const KParams& p, const uint32_t (&
 template <typename S, bool ODD, int FK, bool HO>
 __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5))
     k_stream_collide_x2(KParams p, PairDims pd, S* __restrict__ f) {
-    constexpr bool HALO = ODD || FK == FK_SHAN_CHEN;
     const unsigned full = 0xffffffffu;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t G = blockIdx.x * X2_BLOCK + threadIdx.x;
+    if (G >= pd.pairs) return;  // a whole warp past the last pair (pairs is a multiple of 32)
+    const PairMap pm = map_pair(p, pd, G);
     const uint32_t nx = p.nx, ny = p.ny, nz = p.nz;
-    const PairMap pm = map_pair<HALO>(p, pd);
-    if (!pm.live) return;  // a whole warp past the last row
-    const bool owner = pm.owner;
     const uint32_t x0 = 2 * pm.pair;
     const uint32_t y = pm.y, z = pm.z;
     const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
@@ -331,24 +356,44 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5))
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) row[a][b] = reinterpret_cast<char*>(f) + (uint64_t)(zo[a] + yo[b] + x0) * sizeof(S);
+    // the x neighbour outside the warp: x0 - 1 for lane 0, x0 + 2 for lane 31 (periodic in the row)
+    const uint32_t xe = lane == 0 ? (x0 == 0 ? nx - 1 : x0 - 1) : (x0 + 2 == nx ? 0 : x0 + 2);
 
     // AA gather
+    uint32_t E = 0;  // odd step: lane j < 18 holds the edge half-word edge_dir(j) of lane 0 / 31
+    if (ODD && lane < 18) {
+        constexpr unsigned long long T0 = pack_edges(0), T1 = pack_edges(1), T2 = pack_edges(2);
+        const unsigned long long t = lane < 6 ? T0 : (lane < 12 ? T1 : T2);
+        const uint32_t e = (uint32_t)(t >> (9 * (lane % 6))) & 511u;
+        const int dy = (int)((e >> 5) & 3u) - 1, dz = (int)((e >> 7) & 3u) - 1;
+        const uint32_t x00 = x0 - 2 * lane;          // x0 of lane 0
+        const uint32_t x031 = x00 + 62;              // x0 of lane 31
+        const uint32_t xs = lane < 9 ? (x00 == 0 ? nx - 1 : x00 - 1) : (x031 + 2 == nx ? 0 : x031 + 2);
+        const uint32_t ys = dy > 0 ? yo[0] : (dy < 0 ? yo[2] : yo[1]);  // source row y - dy
+        const uint32_t zs = dz > 0 ? zo[0] : (dz < 0 ? zo[2] : zo[1]);
+        E = ld_half(reinterpret_cast<const char*>(f) + (PB * (e & 31u) + (uint64_t)(zs + ys + xs) * sizeof(S)));
+    }
     V2 g[27];
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         uint32_t w;
         if (!ODD) {
-            w = ld_word(row[1][1], PB, i);
+            w = ld_word(row[1][1] + PB * i);
         } else {
             // f_i(x) sits in slot opp(i) of x - c_i
-            const int dx = -dir_x(i);
-            const uint32_t own = ld_word(row[1 - dir_z(i)][1 - dir_y(i)], PB, dir_opp(i));
-            if (dx == 0) {
+            const uint32_t own = ld_word(row[1 - dir_z(i)][1 - dir_y(i)] + PB * dir_opp(i));
+            if (dir_x(i) == 0) {
                 w = own;
-            } else if (dx < 0) {  // sources x0 - 1 (left lane's high half), x0
-                w = __byte_perm(__shfl_up_sync(full, own, 1), own, 0x5432);
-            } else {  // sources x0 + 1, x0 + 2 (right lane's low half)
-                w = __byte_perm(own, __shfl_down_sync(full, own, 1), 0x5432);
+            } else if (dir_x(i) > 0) {  // sources x0 - 1 (the left neighbour's node 1), x0
+                uint32_t l = __shfl_up_sync(full, own, 1);
+                const uint32_t e = __shfl_sync(full, E, edge_rank(i));
+                if (lane == 0) l = e << 16;
+                w = __byte_perm(l, own, 0x5432);
+            } else {  // sources x0 + 1, x0 + 2 (the right neighbour's node 0)
+                uint32_t r = __shfl_down_sync(full, own, 1);
+                const uint32_t e = __shfl_sync(full, E, 9 + edge_rank(i));
+                if (lane == 31) r = e;
+                w = __byte_perm(own, r, 0x5432);
             }
         }
         g[i] = Pair<S>::unpack(w);
@@ -367,34 +412,57 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5))
         Fy = V2{*reinterpret_cast<const float2*>(p.fy + self)};
         Fz = V2{*reinterpret_cast<const float2*>(p.fz + self)};
     } else {
-        shan_chen_x2(p, yo, zo, x0, Fx, Fy, Fz);
+        shan_chen_x2(p, yo, zo, x0, lane, xe, Fx, Fy, Fz);
     }
     const Macro2 m = collide_direct_x2<HO>(g, Fx, Fy, Fz, p.omega, p.rho0, p.ce, p.cf);
     {
         const V2 u2 = fma2(m.ux, m.ux, fma2(m.uy, m.uy, m.uz * m.uz));
-        const bool bad = owner && (!(m.rho.v.x > 0.0f) || !(m.rho.v.y > 0.0f) || !(u2.v.x < 1.0f) || !(u2.v.y < 1.0f));
+        const bool bad = !(m.rho.v.x > 0.0f) || !(m.rho.v.y > 0.0f) || !(u2.v.x < 1.0f) || !(u2.v.y < 1.0f);
         if (__any_sync(full, bad)) {
             if (bad) atomicOr(p.flag, 1u);
         }
     }
 
-    // AA scatter
+    // AA scatter (w: f*_i of node x0 in the low half, of x0 + 1 in the high half).  At the edges
+    // lane 0 stores f*_i(x0) and lane 31 f*_i(x0 + 1) as half-words: into the half of the own
+    // word that the neighbour outside the warp does not fill, or into that neighbour's word.
+    // row pointers again, from values the compiler cannot tie to the ones above (so that it does
+    // not keep nine 64-bit pointers live through the collision)
+    const uint32_t x0s = ODD ? opaque(x0) : x0;
+    if (ODD) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                row[a][b] = reinterpret_cast<char*>(f) + (uint64_t)(zo[a] + yo[b] + x0s) * sizeof(S);
+    }
+    const uint32_t ls = opaque(lane), xes = opaque(xe);
+    const long long eP = ls == 0 ? (long long)sizeof(S) : ((long long)xes - x0s) * (long long)sizeof(S);  // c_x = +1
+    const long long eM = ls == 0 ? ((long long)xes - x0s) * (long long)sizeof(S) : 0;                   // c_x = -1
+    const bool edge = ls == 0 || ls == 31;
+    const uint32_t hsel = ls == 0 ? 0x4410u : 0x4432u;  // the half that lane 0 / lane 31 stores at the edge
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         const uint32_t w = Pair<S>::pack(g[i]);
         if (!ODD) {
-            if (owner) st_word(row[1][1], PB, dir_opp(i), w);
+            st_word(row[1][1] + PB * dir_opp(i), w);
         } else {
             // f*_i goes to slot i of x + c_i
-            const int dx = dir_x(i);
-            uint32_t v;
-            if (dx == 0)
-                v = w;
-            else if (dx > 0)  // the pair at x0 receives (left lane's node 1, own node 0)
-                v = __byte_perm(__shfl_up_sync(full, w, 1), w, 0x5432);
-            else  // the pair at x0 receives (own node 1, right lane's node 0)
-                v = __byte_perm(w, __shfl_down_sync(full, w, 1), 0x5432);
-            if (owner) st_word(row[1 + dir_z(i)][1 + dir_y(i)], PB, i, v);
+            char* a = row[1 + dir_z(i)][1 + dir_y(i)] + PB * i;
+            if (dir_x(i) == 0) {
+                st_word(a, w);
+            } else {
+                const uint32_t h = __byte_perm(w, 0u, hsel);
+                if (dir_x(i) > 0) {  // the pair at x0 receives f*_i(x0 - 1), f*_i(x0)
+                    const uint32_t v = __byte_perm(__shfl_up_sync(full, w, 1), w, 0x5432);
+                    st_word_if(a, v, ls != 0);
+                    st_half_if(a + eP, h, edge);
+                } else {  // the pair at x0 receives f*_i(x0 + 1), f*_i(x0 + 2)
+                    const uint32_t v = __byte_perm(w, __shfl_down_sync(full, w, 1), 0x5432);
+                    st_word_if(a, v, ls != 31);
+                    st_half_if(a + eM, h, edge);
+                }
+            }
         }
     }
 }

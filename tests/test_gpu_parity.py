@@ -408,9 +408,11 @@ def test_hermite_orders_rejected():
     s.set_model("M1")
 
 
-# Shapes that take the two-nodes-per-thread kernel (16-bit storage, periodic, even nx): one block;
-# a warp with a single pair after a full one; two blocks with a partial one; the smallest row.
-PAIR_SHAPES = [(20, 13, 11), (66, 5, 4), (300, 4, 3), (2, 5, 3)]
+# Shapes that take the two-nodes-per-thread kernel (16-bit storage, periodic, nx a multiple of
+# 64, so that a warp holds 32 pairs of one row): one warp per row (both edge lanes wrap within
+# it); a single row; two and three warps per row, with blocks of 128 pairs spanning rows; five
+# warps per row.
+PAIR_SHAPES = [(64, 5, 3), (64, 1, 1), (128, 3, 2), (192, 2, 3), (320, 2, 2)]
 
 
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
@@ -442,9 +444,9 @@ def test_pair_kernel_steps_match_oracle(orc, name, shape, storage):
 @pytest.mark.parametrize("orders", [(6, 2), (2, 2)], ids=["M4", "M5"])
 @pytest.mark.parametrize("name", ["field", "shan_chen"])
 def test_pair_kernel_hermite_orders_match_oracle(orc, name, orders):
-    """M4 / M5 through the two-nodes-per-thread kernel (FP16, 66 x 5 x 4) against the oracle's
+    """M4 / M5 through the two-nodes-per-thread kernel (FP16, 128 x 5 x 4) against the oracle's
     literal collision, from a state with |u| ~ 0.1."""
-    nx, ny, nz = 66, 5, 4
+    nx, ny, nz = 128, 5, 4
     eq, fo = orders
     g = _moving_state(orc, nx, ny, nz, seed=41)
     kw, okw = dict(nu=0.05), dict(nu=0.05, collision=orc.COLL_LITERAL)
