@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "D3Q27 CM-LBM MLUPS & HBM roofline fraction; time-to-steady warm vs plain"
-PROFILE_EVERY = 8  # kernel times of the step pairs t = 0, 1 (mod 8) are recorded inside the timed region
+PROFILE_EVERY = 32  # kernel times of the step pairs t = 0, 1 (mod 32) are recorded inside the timed region
 BYTES_PER_NODE = {"fp32": 216, "fp16": 108, "bf16": 108}  # AA in place: 27 reads + 27 writes
 
 WORKLOADS = {

@@ -39,7 +39,15 @@ __host__ __device__ constexpr int dir_opp(int i) {
 __host__ __device__ constexpr float w1(int c) { return c == 0 ? 2.0f / 3.0f : 1.0f / 6.0f; }
 __host__ __device__ constexpr float weight(int i) { return w1(dir_x(i)) * w1(dir_y(i)) * w1(dir_z(i)); }
 
+// The y and z components of the 27 directions, 2 bits each (c + 1), for lookups by a runtime index.
+__host__ __device__ constexpr unsigned long long pack_dir(int axis) {
+    unsigned long long c = 0;
+    for (int i = 0; i < 27; ++i) c |= (unsigned long long)((axis == 1 ? dir_y(i) : dir_z(i)) + 1) << (2 * i);
+    return c;
+}
+
 constexpr uint32_t SOLID_BIT = 1u << 31;  // in a link word: the node itself is solid
+constexpr int BLOCK_X = 128;              // one-node kernels: threads per block, one node each along x
 
 // Division by a fixed divisor d >= 1 for dividends n < 2^31 without an integer divide:
 // q = umulhi(n, m) >> s, m = ceil(2^(31 + l) / d), s = l - 1, l = ceil(log2 d); exact because
@@ -101,6 +109,8 @@ struct KParams {
     long long local_off;   // z0 * nx * ny: store node index minus caller (local) node index
     int ho;                // 1: second-order Hermite truncation of f^eq and/or F_i (models M4, M5)
     float ce, cf;          // weights of hermite2_correction (1 / 0 and 1/2 / 0)
+    int pf;                // one-node stream-collide: L2 prefetch distance in blocks of the launch (0: off)
+    FastDiv pf_gx, pf_ny;  // its grid's x blocks per row and rows per plane
 };
 
 // Node coordinates and the offsets of its 26 neighbours with periodic wrap in x, y, z.
