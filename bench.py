@@ -28,6 +28,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "D3Q27 CM-LBM MLUPS & HBM roofline fraction; time-to-steady warm vs plain"
 PROFILE_EVERY = 32  # kernel times of the step pairs t = 0, 1 (mod 32) are recorded inside the timed region
+
+
+def profile_every(steps):
+    """Sampling interval of the kernel-time events: every 32nd step pair on long runs, every pair
+    on runs too short to contain eight sampled pairs."""
+    return PROFILE_EVERY if steps >= 8 * PROFILE_EVERY else 2
 BYTES_PER_NODE = {"fp32": 216, "fp16": 108, "bf16": 108}  # AA in place: 27 reads + 27 writes
 
 WORKLOADS = {
@@ -455,7 +461,7 @@ def run_ours(args, wl):
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
-    s.profile(PROFILE_EVERY)
+    s.profile(profile_every(args.steps))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     s.step(args.steps)
@@ -520,7 +526,9 @@ def run_ours(args, wl):
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
     bpn = CG_BYTES_PER_NODE if cg else (MHD_BYTES_PER_NODE if mhd else BYTES_PER_NODE[args.storage])
-    coll_avg_ms = prof["collide_ms"] / max(1, prof["collide_launches"])
+    if not prof["collide_launches"]:
+        raise RuntimeError("no stream-collide launch was timed inside the timed region")
+    coll_avg_ms = prof["collide_ms"] / prof["collide_launches"]
     achieved = bpn * nodes / (coll_avg_ms * 1e-3) / 1e9
     traffic = committed_traffic(args.workload, args.storage) if args.n in (None, WORKLOADS[args.workload]["n"]) else None
     # every kernel launched in the timed region: one stream-collide per step, plus psi (Shan-Chen)

@@ -28,6 +28,7 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int sms = 0;  // streaming multiprocessors of the device
+    int l2 = 0;   // L2 bytes of the device
 
     void* f = nullptr;  // population store
     bool own_f = false;
@@ -142,8 +143,10 @@ KParams make_params(const lbm_ctx* c) {
     p.ce = c->eq_order == 2 ? 1.0f : 0.0f;
     p.cf = c->force_order == 2 ? 0.5f : 0.0f;
     p.ho = (c->eq_order == 2 || c->force_order == 2) ? 1 : 0;
-    // the one-node stream-collide kernel prefetches the rows of the block two per SM ahead
-    p.pf = 2 * c->sms;
+    // the stream-collide kernels prefetch the rows of the block two per SM ahead, when the
+    // population store does not fit in L2 (a store that fits is read from L2 anyway)
+    const double store_bytes = 27.0 * (double)c->N * (double)elem_size(c->storage);
+    p.pf = store_bytes > (double)c->l2 ? 2 * c->sms : 0;
     p.pf_gx = make_fastdiv((uint32_t)((c->nx + BLOCK_X - 1) / BLOCK_X));
     p.pf_ny = make_fastdiv((uint32_t)c->ny);
     return p;
@@ -374,6 +377,7 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
     cudaError_t e = cudaGetDevice(&c->device);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaGetDevice"));
     e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->l2, cudaDevAttrL2CacheSize, c->device);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaDeviceGetAttribute"));
 
     const size_t bytes = lbm_store_bytes(d);

@@ -113,6 +113,35 @@ struct KParams {
     FastDiv pf_gx, pf_ny;  // its grid's x blocks per row and rows per plane
 };
 
+// L2 prefetch for K1: the block p.pf places later in launch order will gather 27 row segments of
+// BLOCK_X nodes (on an odd step plane k comes from the row shifted by c_k, the source x - c_i of
+// direction i = opp(k)); one thread per 128-byte line of them issues a prefetch.  This keeps more
+// DRAM requests in flight than the gathers alone, which are latency-bound at 16-20 warps per SM.
+template <typename S, bool ODD>
+__device__ __forceinline__ void k1_prefetch(const KParams& p, const S* f) {
+    constexpr uint32_t LPR = BLOCK_X * sizeof(S) / 128;  // lines per row segment
+    const uint32_t t = threadIdx.x;
+    if (t >= 27 * LPR) return;
+    const uint32_t gx = gridDim.x;
+    const uint32_t b = blockIdx.x + gx * (blockIdx.y + gridDim.y * blockIdx.z) + (uint32_t)p.pf;
+    if (b >= gx * gridDim.y * gridDim.z) return;
+    const uint32_t r = p.pf_gx.div(b);
+    const uint32_t zb = p.pf_ny.div(r);
+    int yk = (int)(r - zb * (uint32_t)p.ny), zk = (int)zb + p.z0;
+    const uint32_t k = t / LPR;
+    const uint32_t xs = (b - r * gx) * BLOCK_X + (t - k * LPR) * (128 / sizeof(S));
+    if (xs >= (uint32_t)p.nx) return;
+    if (ODD) {
+        constexpr unsigned long long CY = pack_dir(1), CZ = pack_dir(2);
+        yk += (int)((CY >> (2 * k)) & 3ull) - 1;
+        zk += (int)((CZ >> (2 * k)) & 3ull) - 1;
+        yk = yk < 0 ? p.ny - 1 : (yk >= p.ny ? 0 : yk);
+        zk = zk < 0 ? p.nz - 1 : (zk >= p.nz ? 0 : zk);
+    }
+    const S* a = f + (unsigned long long)p.N * k + ((unsigned long long)zk * p.ny + yk) * p.nx + xs;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 // Node coordinates and the offsets of its 26 neighbours with periodic wrap in x, y, z.
 struct Nbr {
     uint32_t xo[3];  // x - 1, x, x + 1

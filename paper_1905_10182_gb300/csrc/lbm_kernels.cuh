@@ -24,35 +24,6 @@ __device__ __forceinline__ void check_node(const KParams& p, const Macro& m) {
 // K1: one fused AA stream-collide step.  TRACE replaces the collision by the identity, which
 // turns the step into pure streaming with bounce-back (used to check indices bit-exactly).
 // HO: the second-order Hermite truncations (models M4, M5 of Sec. III) instead of the complete ones.
-// L2 prefetch for K1: the block p.pf places later in launch order will gather 27 row segments of
-// BLOCK_X nodes (on an odd step plane k comes from the row shifted by c_k, the source x - c_i of
-// direction i = opp(k)); one thread per 128-byte line of them issues a prefetch.  This keeps more
-// DRAM requests in flight than the gathers alone, which are latency-bound at 16-20 warps per SM.
-template <typename S, bool ODD>
-__device__ __forceinline__ void k1_prefetch(const KParams& p, const S* f) {
-    constexpr uint32_t LPR = BLOCK_X * sizeof(S) / 128;  // lines per row segment
-    const uint32_t t = threadIdx.x;
-    if (t >= 27 * LPR) return;
-    const uint32_t gx = gridDim.x;
-    const uint32_t b = blockIdx.x + gx * (blockIdx.y + gridDim.y * blockIdx.z) + (uint32_t)p.pf;
-    if (b >= gx * gridDim.y * gridDim.z) return;
-    const uint32_t r = p.pf_gx.div(b);
-    const uint32_t zb = p.pf_ny.div(r);
-    int yk = (int)(r - zb * (uint32_t)p.ny), zk = (int)zb + p.z0;
-    const uint32_t k = t / LPR;
-    const uint32_t xs = (b - r * gx) * BLOCK_X + (t - k * LPR) * (128 / sizeof(S));
-    if (xs >= (uint32_t)p.nx) return;
-    if (ODD) {
-        constexpr unsigned long long CY = pack_dir(1), CZ = pack_dir(2);
-        yk += (int)((CY >> (2 * k)) & 3ull) - 1;
-        zk += (int)((CZ >> (2 * k)) & 3ull) - 1;
-        yk = yk < 0 ? p.ny - 1 : (yk >= p.ny ? 0 : yk);
-        zk = zk < 0 ? p.nz - 1 : (zk >= p.nz ? 0 : zk);
-    }
-    const S* a = f + (unsigned long long)p.N * k + ((unsigned long long)zk * p.ny + yk) * p.nx + xs;
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
-}
-
 template <typename S, bool ODD, bool LINKS, int FK, bool TRACE, bool HO>
 __global__ void __launch_bounds__(BLOCK_X, (sizeof(S) == 4 ? 4 : 5)) k_stream_collide(KParams p, S* __restrict__ f) {
     const int x = blockIdx.x * BLOCK_X + threadIdx.x;

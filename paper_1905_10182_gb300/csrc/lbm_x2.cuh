@@ -333,11 +333,35 @@ __device__ __forceinline__ void shan_chen_x2(const KParams& p, const uint32_t (&
     Fz = a * sz;
 }
 
+// L2 prefetch as in the one-node kernel (k1_prefetch): the 27 x 4 lines (one per warp of 32
+// pairs and plane) that the block p.pf places later will gather, one per thread.
+template <typename S, bool ODD>
+__device__ __forceinline__ void x2_prefetch(const KParams& p, const PairDims& pd, const S* f) {
+    const uint32_t t = threadIdx.x;
+    if (t >= 27 * (X2_BLOCK / 32)) return;
+    const uint32_t k = t / (X2_BLOCK / 32), w = t - k * (X2_BLOCK / 32);
+    const uint32_t G = (blockIdx.x + (uint32_t)p.pf) * X2_BLOCK + 32 * w;  // first pair of a warp
+    if (G >= pd.pairs) return;
+    const uint32_t row = pd.np.div(G);
+    const uint32_t zr = pd.ny.div(row);
+    int yk = (int)(row - zr * (uint32_t)p.ny), zk = (int)zr + p.z0;
+    if (ODD) {
+        constexpr unsigned long long CY = pack_dir(1), CZ = pack_dir(2);
+        yk += (int)((CY >> (2 * k)) & 3ull) - 1;
+        zk += (int)((CZ >> (2 * k)) & 3ull) - 1;
+        yk = yk < 0 ? p.ny - 1 : (yk >= p.ny ? 0 : yk);
+        zk = zk < 0 ? p.nz - 1 : (zk >= p.nz ? 0 : zk);
+    }
+    const S* a = f + (unsigned long long)p.N * k + ((unsigned long long)zk * p.ny + yk) * p.nx + 2 * (G - row * pd.np.d);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 template <typename S, bool ODD, int FK, bool HO>
 __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5))
     k_stream_collide_x2(KParams p, PairDims pd, S* __restrict__ f) {
     const unsigned full = 0xffffffffu;
     const uint32_t lane = threadIdx.x & 31u;
+    if (p.pf) x2_prefetch<S, ODD>(p, pd, f);
     const uint32_t G = blockIdx.x * X2_BLOCK + threadIdx.x;
     if (G >= pd.pairs) return;  // a whole warp past the last pair (pairs is a multiple of 32)
     const PairMap pm = map_pair(p, pd, G);
