@@ -166,8 +166,8 @@ template <typename S, bool ODD, bool LINKS, bool HO>
 static cudaError_t launch_step_t(const KParams& p, S* f, int fk, bool trace, cudaStream_t st) {
     const dim3 grid = node_grid(p), block(BLOCK_X);
     if constexpr (sizeof(S) == 2 && !LINKS) {
-        // 16-bit storage, fully periodic, nx a multiple of 64, 4-byte aligned store: two nodes per thread
-        if (!trace && p.nx % 64 == 0 && (reinterpret_cast<uintptr_t>(f) & 3) == 0) {
+        // 16-bit storage, fully periodic, even nx, 4-byte aligned store: two nodes per thread
+        if (!trace && p.nx % 2 == 0 && (reinterpret_cast<uintptr_t>(f) & 3) == 0) {
             const dim3 grid2 = x2_grid(p);
             const PairDims pd = make_pair_dims(p);
             switch (fk) {

@@ -2,10 +2,10 @@
 // (no walls, no mask) with an even nx: the same step as k_stream_collide (AA pattern, direct-form
 // collision of Sec. II, optional second-order Hermite truncations), restructured for the 16-bit
 // kernel's real limit, instruction issue rather than HBM bandwidth:
-//  * each population of the node pair (x, x + 1), x even, moves as one 32-bit word (two 16-bit
-//    values): one load and one store per direction for two nodes;
-//  * on the odd step the values of the +-x neighbours come from the adjacent lane by a warp
-//    shuffle; only the lanes at a warp edge (and the periodic wrap) touch a single 16-bit value;
+//  * the populations of a node pair move as aligned 32-bit words (two 16-bit values): on even
+//    steps the pair (x, x + 1), x even, one load and one store per direction; on odd steps the
+//    pair (x - 1, x), whose sources and targets are aligned words for the 18 directions with
+//    c_x = +-1 (the other 9 take two loads and two 16-bit stores);
 //  * the collision runs on packed FP32 pairs (__fadd2_rn / __fmul2_rn / __ffma2_rn), one
 //    instruction for both nodes.
 // Included by lbm_kernels.cuh.
@@ -206,19 +206,18 @@ __device__ __forceinline__ Macro2 collide_direct_x2(V2 (&g)[27], V2 Fx, V2 Fy, V
 }
 
 // ----------------------------------------------------------------------------- the kernel
-// Thread -> node pair (x0 = 2 pair, x0 + 1) of a row (y, z): the pairs of all rows are numbered
-// row by row and thread G of the grid owns pair G.  The kernel is used for nx a multiple of 64, so
-// that every warp holds 32 pairs of one row: lane 0 and lane 31 are the only lanes whose x
-// neighbour pair (on the left, on the right; periodic in the row) is in another warp.
-//
-// The x neighbours (odd steps; the psi stencil of Shan-Chen) come from the adjacent lane by a warp
-// shuffle.  At the two edges of a warp the half-words are read and written directly, and only by
-// the warp whose nodes they belong to in the AA pattern: the 18 half-words that lanes 0 and 31
-// gather from outside the warp are loaded by lanes 0..17 in one instruction and passed on by
-// shuffles, and the half-words that lanes 0 and 31 scatter outside their own 32-bit words are
-// stored with 16-bit stores.  Every population slot is thus read and written only by the warp
-// that owns its node (no thread recomputes a node of another warp, whose slots that warp
-// overwrites), so the in-place update is race free in any order of the warps.
+// Thread -> node pair of a row (y, z): the pairs of all rows are numbered row by row, thread G of
+// the grid takes pair p = G of its row (nx even).  The words of the store are the aligned pairs
+// W(q) = (2q, 2q + 1).
+//  * Even steps (every node reads and writes its own slots): the thread owns nodes (2p, 2p + 1),
+//    the word W(p) of each plane.
+//  * Odd steps: the thread owns the odd-aligned pair A = 2p - 1, B = 2p (A = nx - 1 for p = 0).
+//    The gathered sources and the scattered targets of the 18 directions with c_x = +-1 are then
+//    the aligned words W(p - 1) and W(p); for c_x = 0 the two nodes straddle W(p - 1) and W(p),
+//    which takes two loads and a byte permute, and two 16-bit stores.
+// A thread so reads and writes only the slots of its own nodes (the other half of a word it
+// loads belongs to another node and is not used): no thread recomputes another's node, no value
+// crosses lanes, and the in-place update is race free in any order of the threads.
 struct PairMap {
     uint32_t pair, y, z;
 };
@@ -246,50 +245,37 @@ inline dim3 x2_grid(const KParams& p) {
     return dim3((make_pair_dims(p).pairs + X2_BLOCK - 1) / X2_BLOCK, 1, 1);
 }
 
-// Edge loads of the gather: lane j < 9 loads for lane 0 the half-word of the j-th direction with
-// c_x = +1 (source x0 - 1), lane 9 + j for lane 31 that of the j-th direction with c_x = -1
-// (source x0 + 2).  edge_dir(j): that direction; edge_rank(i): the position of direction i among
-// the directions with its c_x.
-__host__ __device__ constexpr int edge_rank(int i) {
-    int n = 0;
-    for (int k = 0; k < i; ++k)
-        if (dir_x(k) == dir_x(i)) ++n;
-    return n;
-}
-__host__ __device__ constexpr int edge_dir(int j) {
-    const int cx = j < 9 ? 1 : -1, r = j < 9 ? j : j - 9;
-    for (int i = 0; i < 27; ++i)
-        if (dir_x(i) == cx && edge_rank(i) == r) return i;
-    return 0;
-}
-// six lanes per word, 9 bits each: the slot opp(d) (5 bits), dy + 1, dz + 1 (2 bits each) of d = edge_dir(j)
-__host__ __device__ constexpr unsigned long long pack_edges(int part) {
-    unsigned long long c = 0;
-    for (int e = 0; e < 6; ++e) {
-        const int d = edge_dir(6 * part + e);
-        c |= (unsigned long long)(dir_opp(d) | (dir_y(d) + 1) << 5 | (dir_z(d) + 1) << 7) << (9 * e);
+// L2 prefetch as in the one-node kernel (k1_prefetch): the 27 x 4 lines (one per 32 pairs and
+// plane) that the block p.pf places later will gather, one per thread (each 32 pairs lie in one
+// row when nx is a multiple of 64; otherwise a line may cover the start of the next row, and the
+// prefetch only misses part of it).
+template <typename S, bool ODD>
+__device__ __forceinline__ void x2_prefetch(const KParams& p, const PairDims& pd, const S* f) {
+    const uint32_t t = threadIdx.x;
+    if (t >= 27 * (X2_BLOCK / 32)) return;
+    const uint32_t k = t / (X2_BLOCK / 32), w = t - k * (X2_BLOCK / 32);
+    const uint32_t G = (blockIdx.x + (uint32_t)p.pf) * X2_BLOCK + 32 * w;
+    if (G >= pd.pairs) return;
+    const uint32_t row = pd.np.div(G);
+    const uint32_t zr = pd.ny.div(row);
+    int yk = (int)(row - zr * (uint32_t)p.ny), zk = (int)zr + p.z0;
+    if (ODD) {
+        constexpr unsigned long long CY = pack_dir(1), CZ = pack_dir(2);
+        yk += (int)((CY >> (2 * k)) & 3ull) - 1;
+        zk += (int)((CZ >> (2 * k)) & 3ull) - 1;
+        yk = yk < 0 ? p.ny - 1 : (yk >= p.ny ? 0 : yk);
+        zk = zk < 0 ? p.nz - 1 : (zk >= p.nz ? 0 : zk);
     }
-    return c;
+    const S* a = f + (unsigned long long)p.N * k + ((unsigned long long)zk * p.ny + yk) * p.nx + 2 * (G - row * pd.np.d);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
 }
 
-// The 32-bit word of plane k at a row pointer: row + k * PB, PB = N * sizeof(S) bytes per plane.
-// Row pointers (one per (y, z) offset of the node pair, 64-bit) are formed once per thread, so
-// each access costs one 64-bit add of a constant plane offset.
+// 32-bit words and 16-bit halves of the store at byte addresses.  Row pointers (one per (y, z)
+// offset of the pair, 64-bit) are formed once per thread, so that an access costs one 64-bit add
+// of a constant plane offset (k N sizeof(S) bytes).
 __device__ __forceinline__ uint32_t ld_word(const char* a) { return *reinterpret_cast<const uint32_t*>(a); }
 __device__ __forceinline__ void st_word(char* a, uint32_t w) { *reinterpret_cast<uint32_t*>(a) = w; }
-// one 16-bit storage value (an edge half-word)
-__device__ __forceinline__ uint32_t ld_half(const char* a) { return *reinterpret_cast<const unsigned short*>(a); }
-// stores under a per-lane predicate, written as predicated instructions (no branch around them)
-__device__ __forceinline__ void st_word_if(char* a, uint32_t w, bool q) {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p st.global.b32 [%0], %1;\n\t}" ::"l"(a), "r"(w),
-                 "r"((uint32_t)q)
-                 : "memory");
-}
-__device__ __forceinline__ void st_half_if(char* a, uint32_t h, bool q) {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p st.global.b16 [%0], %1;\n\t}" ::"l"(a),
-                 "h"((unsigned short)h), "r"((uint32_t)q)
-                 : "memory");
-}
+__device__ __forceinline__ void st_half(char* a, uint32_t h) { *reinterpret_cast<unsigned short*>(a) = (unsigned short)h; }
 // the value unchanged, opaque to the compiler (keeps it from holding values derived from it)
 __device__ __forceinline__ uint32_t opaque(uint32_t v) {
     asm volatile("mov.b32 %0, %0;" : "+r"(v));
@@ -297,26 +283,31 @@ __device__ __forceinline__ uint32_t opaque(uint32_t v) {
 }
 
 // Shan-Chen force on the pair: F = -G psi(x) sum_i w_i c_i psi(x + c_i) (Sec. III, static
-// droplet); psi(x0 - 1) and psi(x0 + 2) by shuffle, loaded by lanes 0 and 31 (psi is read only).
+// droplet).  psi of the nodes x - 1, x, x + 1 of the pair from the aligned float2 words of the
+// row (psi is read only): even pairs (2p, 2p + 1) take the words at 2p - 2, 2p, 2p + 2; odd pairs
+// (2p - 1, 2p) those at 2p - 2, 2p (x0 = 2p, xl / xr = x0 -+ 2, periodic in the row).
+template <bool ODD>
 __device__ __forceinline__ void shan_chen_x2(const KParams& p, const uint32_t (&yo)[3], const uint32_t (&zo)[3],
-                                             uint32_t x0, uint32_t lane, uint32_t xe, V2& Fx, V2& Fy, V2& Fz) {
-    const unsigned full = 0xffffffffu;
+                                             uint32_t x0, uint32_t xl, uint32_t xr, V2& Fx, V2& Fy, V2& Fz) {
     V2 sx = bc(0.0f), sy = bc(0.0f), sz = bc(0.0f), self = bc(0.0f);
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
             const float* r = p.psi + zo[dz + 1] + yo[dy + 1];
-            const float2 c = *reinterpret_cast<const float2*>(r + x0);
-            float e = 0.0f;
-            if (lane == 0 || lane == 31) e = r[xe];
-            float left = __shfl_up_sync(full, c.y, 1);    // psi(x0 - 1)
-            float right = __shfl_down_sync(full, c.x, 1);  // psi(x0 + 2)
-            if (lane == 0) left = e;
-            if (lane == 31) right = e;
-            const V2 m = V2{make_float2(left, c.x)};    // psi(x - 1) of the pair
-            const V2 z0 = V2{c};                        // psi(x)
-            const V2 pl = V2{make_float2(c.y, right)};  // psi(x + 1)
+            const float2 L = __ldg(reinterpret_cast<const float2*>(r + xl));
+            const float2 c = __ldg(reinterpret_cast<const float2*>(r + x0));
+            V2 m, z0, pl;  // psi(x - 1), psi(x), psi(x + 1) of the pair's two nodes
+            if (ODD) {
+                m = V2{L};
+                z0 = V2{make_float2(L.y, c.x)};
+                pl = V2{c};
+            } else {
+                const float2 R = __ldg(reinterpret_cast<const float2*>(r + xr));
+                m = V2{make_float2(L.y, c.x)};
+                z0 = V2{c};
+                pl = V2{make_float2(c.y, R.x)};
+            }
             const float wyz = w1(dy) * w1(dz);
             sx = fma2(bc(wyz * w1(1)), pl - m, sx);
             if (dy != 0 || dz != 0) {
@@ -333,37 +324,12 @@ __device__ __forceinline__ void shan_chen_x2(const KParams& p, const uint32_t (&
     Fz = a * sz;
 }
 
-// L2 prefetch as in the one-node kernel (k1_prefetch): the 27 x 4 lines (one per warp of 32
-// pairs and plane) that the block p.pf places later will gather, one per thread.
-template <typename S, bool ODD>
-__device__ __forceinline__ void x2_prefetch(const KParams& p, const PairDims& pd, const S* f) {
-    const uint32_t t = threadIdx.x;
-    if (t >= 27 * (X2_BLOCK / 32)) return;
-    const uint32_t k = t / (X2_BLOCK / 32), w = t - k * (X2_BLOCK / 32);
-    const uint32_t G = (blockIdx.x + (uint32_t)p.pf) * X2_BLOCK + 32 * w;  // first pair of a warp
-    if (G >= pd.pairs) return;
-    const uint32_t row = pd.np.div(G);
-    const uint32_t zr = pd.ny.div(row);
-    int yk = (int)(row - zr * (uint32_t)p.ny), zk = (int)zr + p.z0;
-    if (ODD) {
-        constexpr unsigned long long CY = pack_dir(1), CZ = pack_dir(2);
-        yk += (int)((CY >> (2 * k)) & 3ull) - 1;
-        zk += (int)((CZ >> (2 * k)) & 3ull) - 1;
-        yk = yk < 0 ? p.ny - 1 : (yk >= p.ny ? 0 : yk);
-        zk = zk < 0 ? p.nz - 1 : (zk >= p.nz ? 0 : zk);
-    }
-    const S* a = f + (unsigned long long)p.N * k + ((unsigned long long)zk * p.ny + yk) * p.nx + 2 * (G - row * pd.np.d);
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
-}
-
 template <typename S, bool ODD, int FK, bool HO>
 __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5))
     k_stream_collide_x2(KParams p, PairDims pd, S* __restrict__ f) {
-    const unsigned full = 0xffffffffu;
-    const uint32_t lane = threadIdx.x & 31u;
     if (p.pf) x2_prefetch<S, ODD>(p, pd, f);
     const uint32_t G = blockIdx.x * X2_BLOCK + threadIdx.x;
-    if (G >= pd.pairs) return;  // a whole warp past the last pair (pairs is a multiple of 32)
+    if (G >= pd.pairs) return;
     const PairMap pm = map_pair(p, pd, G);
     const uint32_t nx = p.nx, ny = p.ny, nz = p.nz;
     const uint32_t x0 = 2 * pm.pair;
@@ -374,29 +340,17 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5))
     const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
     const uint32_t zo[3] = {zm * pl, z * pl, zp * pl};
     const uint32_t self = zo[1] + yo[1] + x0;
+    // x of the words W(p - 1), W(p + 1) (periodic in the row)
+    const uint32_t xl = x0 == 0 ? nx - 2 : x0 - 2, xr = x0 + 2 == nx ? 0 : x0 + 2;
     const uint64_t PB = (uint64_t)p.N * sizeof(S);
-    char* row[3][3];  // row[a][b]: the pair's word of plane 0 in row (y + b - 1, z + a - 1)
+    const long long eL = ((long long)xl - (long long)x0) * (long long)sizeof(S);  // W(p - 1) from W(p), bytes
+    char* row[3][3];  // row[a][b]: the word W(p) of plane 0 in row (y + b - 1, z + a - 1)
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) row[a][b] = reinterpret_cast<char*>(f) + (uint64_t)(zo[a] + yo[b] + x0) * sizeof(S);
-    // the x neighbour outside the warp: x0 - 1 for lane 0, x0 + 2 for lane 31 (periodic in the row)
-    const uint32_t xe = lane == 0 ? (x0 == 0 ? nx - 1 : x0 - 1) : (x0 + 2 == nx ? 0 : x0 + 2);
 
-    // AA gather
-    uint32_t E = 0;  // odd step: lane j < 18 holds the edge half-word edge_dir(j) of lane 0 / 31
-    if (ODD && lane < 18) {
-        constexpr unsigned long long T0 = pack_edges(0), T1 = pack_edges(1), T2 = pack_edges(2);
-        const unsigned long long t = lane < 6 ? T0 : (lane < 12 ? T1 : T2);
-        const uint32_t e = (uint32_t)(t >> (9 * (lane % 6))) & 511u;
-        const int dy = (int)((e >> 5) & 3u) - 1, dz = (int)((e >> 7) & 3u) - 1;
-        const uint32_t x00 = x0 - 2 * lane;          // x0 of lane 0
-        const uint32_t x031 = x00 + 62;              // x0 of lane 31
-        const uint32_t xs = lane < 9 ? (x00 == 0 ? nx - 1 : x00 - 1) : (x031 + 2 == nx ? 0 : x031 + 2);
-        const uint32_t ys = dy > 0 ? yo[0] : (dy < 0 ? yo[2] : yo[1]);  // source row y - dy
-        const uint32_t zs = dz > 0 ? zo[0] : (dz < 0 ? zo[2] : zo[1]);
-        E = ld_half(reinterpret_cast<const char*>(f) + (PB * (e & 31u) + (uint64_t)(zs + ys + xs) * sizeof(S)));
-    }
+    // AA gather (odd: nodes A = x0 - 1, B = x0; f_i(x) sits in slot opp(i) of x - c_i)
     V2 g[27];
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
@@ -404,21 +358,13 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5))
         if (!ODD) {
             w = ld_word(row[1][1] + PB * i);
         } else {
-            // f_i(x) sits in slot opp(i) of x - c_i
-            const uint32_t own = ld_word(row[1 - dir_z(i)][1 - dir_y(i)] + PB * dir_opp(i));
-            if (dir_x(i) == 0) {
-                w = own;
-            } else if (dir_x(i) > 0) {  // sources x0 - 1 (the left neighbour's node 1), x0
-                uint32_t l = __shfl_up_sync(full, own, 1);
-                const uint32_t e = __shfl_sync(full, E, edge_rank(i));
-                if (lane == 0) l = e << 16;
-                w = __byte_perm(l, own, 0x5432);
-            } else {  // sources x0 + 1, x0 + 2 (the right neighbour's node 0)
-                uint32_t r = __shfl_down_sync(full, own, 1);
-                const uint32_t e = __shfl_sync(full, E, 9 + edge_rank(i));
-                if (lane == 31) r = e;
-                w = __byte_perm(own, r, 0x5432);
-            }
+            const char* a = row[1 - dir_z(i)][1 - dir_y(i)] + PB * dir_opp(i);
+            if (dir_x(i) > 0)  // sources x0 - 2, x0 - 1: W(p - 1)
+                w = ld_word(a + eL);
+            else if (dir_x(i) < 0)  // sources x0, x0 + 1: W(p)
+                w = ld_word(a);
+            else  // sources x0 - 1, x0: the high half of W(p - 1), the low half of W(p)
+                w = __byte_perm(ld_word(a + eL), ld_word(a), 0x5432);
         }
         g[i] = Pair<S>::unpack(w);
     }
@@ -432,39 +378,38 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5))
         Fx = bc(p.kolm[y]);
         Fy = Fz = bc(0.0f);
     } else if (FK == FK_FIELD) {
-        Fx = V2{*reinterpret_cast<const float2*>(p.fx + self)};
-        Fy = V2{*reinterpret_cast<const float2*>(p.fy + self)};
-        Fz = V2{*reinterpret_cast<const float2*>(p.fz + self)};
+        if (ODD) {
+            const uint32_t sa = zo[1] + yo[1] + (x0 == 0 ? nx - 1 : x0 - 1);
+            Fx = V2{make_float2(p.fx[sa], p.fx[self])};
+            Fy = V2{make_float2(p.fy[sa], p.fy[self])};
+            Fz = V2{make_float2(p.fz[sa], p.fz[self])};
+        } else {
+            Fx = V2{*reinterpret_cast<const float2*>(p.fx + self)};
+            Fy = V2{*reinterpret_cast<const float2*>(p.fy + self)};
+            Fz = V2{*reinterpret_cast<const float2*>(p.fz + self)};
+        }
     } else {
-        shan_chen_x2(p, yo, zo, x0, lane, xe, Fx, Fy, Fz);
+        shan_chen_x2<ODD>(p, yo, zo, x0, xl, xr, Fx, Fy, Fz);
     }
     const Macro2 m = collide_direct_x2<HO>(g, Fx, Fy, Fz, p.omega, p.rho0, p.ce, p.cf);
     {
         const V2 u2 = fma2(m.ux, m.ux, fma2(m.uy, m.uy, m.uz * m.uz));
         const bool bad = !(m.rho.v.x > 0.0f) || !(m.rho.v.y > 0.0f) || !(u2.v.x < 1.0f) || !(u2.v.y < 1.0f);
-        if (__any_sync(full, bad)) {
+        if (__any_sync(__activemask(), bad)) {
             if (bad) atomicOr(p.flag, 1u);
         }
     }
 
-    // AA scatter (w: f*_i of node x0 in the low half, of x0 + 1 in the high half).  At the edges
-    // lane 0 stores f*_i(x0) and lane 31 f*_i(x0 + 1) as half-words: into the half of the own
-    // word that the neighbour outside the warp does not fill, or into that neighbour's word.
-    // row pointers again, from values the compiler cannot tie to the ones above (so that it does
-    // not keep nine 64-bit pointers live through the collision)
-    const uint32_t x0s = ODD ? opaque(x0) : x0;
-    if (ODD) {
+    // AA scatter (w: f*_i of the pair's first node in the low half, of its second in the high half)
+    if (ODD) {  // row pointers again, from a value the compiler cannot tie to the ones above (so
+                // that it does not keep nine 64-bit pointers live through the collision)
+        const uint32_t x0s = opaque(x0);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int b = 0; b < 3; ++b)
                 row[a][b] = reinterpret_cast<char*>(f) + (uint64_t)(zo[a] + yo[b] + x0s) * sizeof(S);
     }
-    const uint32_t ls = opaque(lane), xes = opaque(xe);
-    const long long eP = ls == 0 ? (long long)sizeof(S) : ((long long)xes - x0s) * (long long)sizeof(S);  // c_x = +1
-    const long long eM = ls == 0 ? ((long long)xes - x0s) * (long long)sizeof(S) : 0;                   // c_x = -1
-    const bool edge = ls == 0 || ls == 31;
-    const uint32_t hsel = ls == 0 ? 0x4410u : 0x4432u;  // the half that lane 0 / lane 31 stores at the edge
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         const uint32_t w = Pair<S>::pack(g[i]);
@@ -473,19 +418,13 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5))
         } else {
             // f*_i goes to slot i of x + c_i
             char* a = row[1 + dir_z(i)][1 + dir_y(i)] + PB * i;
-            if (dir_x(i) == 0) {
+            if (dir_x(i) > 0) {  // targets x0, x0 + 1: W(p)
                 st_word(a, w);
-            } else {
-                const uint32_t h = __byte_perm(w, 0u, hsel);
-                if (dir_x(i) > 0) {  // the pair at x0 receives f*_i(x0 - 1), f*_i(x0)
-                    const uint32_t v = __byte_perm(__shfl_up_sync(full, w, 1), w, 0x5432);
-                    st_word_if(a, v, ls != 0);
-                    st_half_if(a + eP, h, edge);
-                } else {  // the pair at x0 receives f*_i(x0 + 1), f*_i(x0 + 2)
-                    const uint32_t v = __byte_perm(w, __shfl_down_sync(full, w, 1), 0x5432);
-                    st_word_if(a, v, ls != 31);
-                    st_half_if(a + eM, h, edge);
-                }
+            } else if (dir_x(i) < 0) {  // targets x0 - 2, x0 - 1: W(p - 1)
+                st_word(a + eL, w);
+            } else {  // targets x0 - 1 (high half of W(p - 1)), x0 (low half of W(p))
+                st_half(a + eL + sizeof(S), w & 0xffffu);
+                st_half(a, w >> 16);
             }
         }
     }

@@ -21,9 +21,9 @@ PATTERN = 0xA5
 
 CASES = [
     ("fp32", (19, 13, 11), {}, None),
-    ("fp16", (128, 5, 4), {}, None),                     # two nodes per thread
-    ("bf16", (64, 13, 11), {}, ("shan_chen", (-5.5,))),  # pair kernel with the psi stencil
-    ("fp16", (66, 5, 4), {}, None),                      # one node per thread (nx not a multiple of 64)
+    ("fp16", (66, 5, 4), {}, None),                      # two nodes per thread
+    ("bf16", (20, 13, 11), {}, ("shan_chen", (-5.5,))),  # pair kernel with the psi stencil
+    ("fp16", (19, 5, 4), {}, None),                      # one node per thread (odd nx)
     ("fp32", (19, 13, 11), {"walls_y": True, "mask": True}, ("uniform", (1e-4, 0, 0))),
     ("fp16", (19, 13, 11), {"walls_y": True}, ("uniform", (1e-4, 0, 0))),
     ("fp32", (20, 12, 10), {}, ("field", None)),

@@ -408,11 +408,11 @@ def test_hermite_orders_rejected():
     s.set_model("M1")
 
 
-# Shapes that take the two-nodes-per-thread kernel (16-bit storage, periodic, nx a multiple of
-# 64, so that a warp holds 32 pairs of one row): one warp per row (both edge lanes wrap within
-# it); a single row; two and three warps per row, with blocks of 128 pairs spanning rows; five
-# warps per row.
-PAIR_SHAPES = [(64, 5, 3), (64, 1, 1), (128, 3, 2), (192, 2, 3), (320, 2, 2)]
+# Shapes that take the two-nodes-per-thread kernel (16-bit storage, periodic, even nx; on odd
+# steps a thread owns the pair (x - 1, x), wrapping at the row start): several rows per warp
+# (nx = 20, 66, 2 -- a single pair per row); one warp per row; blocks of 128 pairs spanning rows
+# (nx = 192); a row of five warps and a partial one (nx = 300).
+PAIR_SHAPES = [(20, 13, 11), (66, 5, 4), (2, 5, 3), (64, 5, 3), (192, 2, 3), (300, 4, 3)]
 
 
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
