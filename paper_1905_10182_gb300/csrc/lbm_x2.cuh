@@ -430,4 +430,53 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5))
     }
 }
 
+// psi = 1 - exp(-rho) of the pair's two nodes (the Shan-Chen pseudo-potential, as k_psi) from the
+// same word gathers as k_stream_collide_x2 (odd steps: the odd-aligned pair), blocks in reverse
+// order like k_psi.  The sum over the 27 values runs in the order of k_psi, so psi is the same to
+// the bit.
+template <typename S, bool ODD>
+__global__ void __launch_bounds__(X2_BLOCK) k_psi_x2(KParams p, PairDims pd, const S* __restrict__ f,
+                                                      float* __restrict__ psi) {
+    const uint32_t G = (gridDim.x - 1 - blockIdx.x) * X2_BLOCK + threadIdx.x;
+    if (G >= pd.pairs) return;
+    const PairMap pm = map_pair(p, pd, G);
+    const uint32_t nx = p.nx, ny = p.ny, nz = p.nz;
+    const uint32_t x0 = 2 * pm.pair;
+    const uint32_t y = pm.y, z = pm.z;
+    const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const uint32_t yo[3] = {ym * nx, y * nx, yp * nx};
+    const uint32_t pl = nx * ny;
+    const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    const uint32_t zo[3] = {zm * pl, z * pl, zp * pl};
+    const uint32_t xl = x0 == 0 ? nx - 2 : x0 - 2;
+    const uint64_t PB = (uint64_t)p.N * sizeof(S);
+    const long long eL = ((long long)xl - (long long)x0) * (long long)sizeof(S);
+    const char* fb = reinterpret_cast<const char*>(f);
+    V2 dr = bc(0.0f);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        uint32_t w;
+        if (!ODD) {
+            w = ld_word(fb + (uint64_t)(zo[1] + yo[1] + x0) * sizeof(S) + PB * i);
+        } else {
+            const char* a = fb + (uint64_t)(zo[1 - dir_z(i)] + yo[1 - dir_y(i)] + x0) * sizeof(S) + PB * dir_opp(i);
+            if (dir_x(i) > 0)
+                w = ld_word(a + eL);
+            else if (dir_x(i) < 0)
+                w = ld_word(a);
+            else
+                w = __byte_perm(ld_word(a + eL), ld_word(a), 0x5432);
+        }
+        dr = dr + Pair<S>::unpack(w);
+    }
+    const float a0 = 1.0f - expf(-(p.rho0 + dr.v.x)), a1 = 1.0f - expf(-(p.rho0 + dr.v.y));
+    const uint32_t self = zo[1] + yo[1] + x0;
+    if (ODD) {
+        psi[zo[1] + yo[1] + (x0 == 0 ? nx - 1 : x0 - 1)] = a0;
+        psi[self] = a1;
+    } else {
+        *reinterpret_cast<float2*>(psi + self) = make_float2(a0, a1);
+    }
+}
+
 }  // namespace cmlbm
