@@ -214,9 +214,9 @@ cudaError_t launch_psi(const KParams& p, const void* f, float* psi, int odd, cud
     const S* fs = static_cast<const S*>(f);
     const dim3 grid = node_grid(p), block(BLOCK_X);
     const bool links = p.links != nullptr;
-    if constexpr (sizeof(S) == 2) {
-        // 16-bit storage, fully periodic, even nx: two nodes per thread, as the stream-collide step
-        if (!links && p.nx % 2 == 0 && (reinterpret_cast<uintptr_t>(f) & 3) == 0) {
+    {
+        // fully periodic, even nx: two nodes per thread, with the word gathers of the pair kernel
+        if (!links && p.nx % 2 == 0 && (reinterpret_cast<uintptr_t>(f) & (2 * sizeof(S) - 1)) == 0) {
             const PairDims pd = make_pair_dims(p);
             if (odd) k_psi_x2<S, true><<<x2_grid(p), X2_BLOCK, 0, st>>>(p, pd, fs, psi);
             else k_psi_x2<S, false><<<x2_grid(p), X2_BLOCK, 0, st>>>(p, pd, fs, psi);

@@ -430,6 +430,24 @@ __global__ void __launch_bounds__(X2_BLOCK, (ODD ? 4 : 5))
     }
 }
 
+// The values of a node pair (2q, 2q + 1) from its aligned word, and of the straddling pair
+// (2q - 1, 2q) from the words at a and b = a + one word: 16-bit pairs as one 32-bit word, FP32
+// pairs as one float2.
+template <typename S>
+__device__ __forceinline__ V2 ld_pair(const char* a) {
+    if constexpr (sizeof(S) == 4)
+        return V2{*reinterpret_cast<const float2*>(a)};
+    else
+        return Pair<S>::unpack(ld_word(a));
+}
+template <typename S>
+__device__ __forceinline__ V2 ld_pair_straddle(const char* a, const char* b) {
+    if constexpr (sizeof(S) == 4)
+        return V2{make_float2(reinterpret_cast<const float2*>(a)->y, reinterpret_cast<const float2*>(b)->x)};
+    else
+        return Pair<S>::unpack(__byte_perm(ld_word(a), ld_word(b), 0x5432));
+}
+
 // psi = 1 - exp(-rho) of the pair's two nodes (the Shan-Chen pseudo-potential, as k_psi) from the
 // same word gathers as k_stream_collide_x2 (odd steps: the odd-aligned pair), blocks in reverse
 // order like k_psi.  The sum over the 27 values runs in the order of k_psi, so psi is the same to
@@ -455,19 +473,19 @@ __global__ void __launch_bounds__(X2_BLOCK) k_psi_x2(KParams p, PairDims pd, con
     V2 dr = bc(0.0f);
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
-        uint32_t w;
+        V2 v;
         if (!ODD) {
-            w = ld_word(fb + (uint64_t)(zo[1] + yo[1] + x0) * sizeof(S) + PB * i);
+            v = ld_pair<S>(fb + (uint64_t)(zo[1] + yo[1] + x0) * sizeof(S) + PB * i);
         } else {
             const char* a = fb + (uint64_t)(zo[1 - dir_z(i)] + yo[1 - dir_y(i)] + x0) * sizeof(S) + PB * dir_opp(i);
             if (dir_x(i) > 0)
-                w = ld_word(a + eL);
+                v = ld_pair<S>(a + eL);
             else if (dir_x(i) < 0)
-                w = ld_word(a);
+                v = ld_pair<S>(a);
             else
-                w = __byte_perm(ld_word(a + eL), ld_word(a), 0x5432);
+                v = ld_pair_straddle<S>(a + eL, a);
         }
-        dr = dr + Pair<S>::unpack(w);
+        dr = dr + v;
     }
     const float a0 = 1.0f - expf(-(p.rho0 + dr.v.x)), a1 = 1.0f - expf(-(p.rho0 + dr.v.y));
     const uint32_t self = zo[1] + yo[1] + x0;
