@@ -1,6 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle, on the same seeded inputs.
 
-Tolerances (FP32 arithmetic on deviations):
+Tolerances (FP32 arithmetic on deviations; each output is a chain of about 30 FP32 operations on
+quantities bounded by S):
   one step:  |g_gpu - g_oracle| <= C * eps32 * S, eps32 = 2^-24, C = 64, where S is the largest
              magnitude entering the deviation-form arithmetic, max(|g|, rho0 |u|, |F|);
   n steps:   n times the one-step bound;
