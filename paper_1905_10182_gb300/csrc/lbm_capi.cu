@@ -52,7 +52,7 @@ struct lbm_ctx {
     // colour-gradient two-phase model (App. D), off unless lbm_set_colour_gradient was called; the
     // store f then holds the red populations (full, not deviations)
     float* cgb = nullptr;  // 27 N: blue populations
-    float* cgf = nullptr;  // 2 N: phi, rho
+    float* cgf = nullptr;  // N (phi, rho) pairs
     CgParams cg{};
 
     float* macro = nullptr;  // 4N: rho, ux, uy, uz (10N with the magnetic field: + b, j; 6N two-phase: + rho_r, rho_b)

@@ -46,7 +46,7 @@ __host__ __device__ constexpr float phi_shell(int i) {
 
 struct CgArgs {
     float* fb;         // blue store
-    float* fld;        // 2 N: phi, rho
+    float* fld;        // N (phi, rho) pairs, interleaved
     float rho_r0, rho_b0, alpha_r, alpha_b, inv_nu_r, inv_nu_b, A, beta;
     float g[3];
     float rho_mid;
@@ -148,8 +148,7 @@ __global__ void __launch_bounds__(CG_BLOCK) k_cg_fields(KParams p, CgArgs q, con
     const uint32_t link = LINKS ? p.links[nb.self()] : 0u;
     float f[27], rr, rb;
     gather_two<ODD, LINKS>(fr, q.fb, p.N, nb, link, f, rr, rb);
-    q.fld[nb.self()] = order_param(q, rr, rb);
-    q.fld[p.N + nb.self()] = rr + rb;
+    reinterpret_cast<float2*>(q.fld)[nb.self()] = make_float2(order_param(q, rr, rb), rr + rb);
 }
 
 template <bool ODD, bool LINKS>
@@ -164,16 +163,16 @@ __global__ void __launch_bounds__(CG_BLOCK, 3) k_cg_step(KParams p, CgArgs q, fl
     gather_two<ODD, LINKS>(fr, q.fb, p.N, nb, link, f, rr, rb);
     const float rho = rr + rb;
     // gradients of phi and rho: (1/cs^2) sum_i w_i c_i X(x + c_i); behind a wall, X(x)
-    const float* phf = q.fld;
-    const float* rhf = q.fld + p.N;
+    const float2* fl = reinterpret_cast<const float2*>(q.fld);  // (phi, rho) of every node
     float gp[3] = {0.0f, 0.0f, 0.0f}, gr[3] = {0.0f, 0.0f, 0.0f};
-    const float ph0 = phf[self], rh0 = rhf[self];
+    const float2 fl0 = fl[self];
+    const float ph0 = fl0.x, rh0 = fl0.y;
 #pragma unroll
     for (int i = 1; i < 27; ++i) {
         const bool behind = LINKS && ((link >> dir_opp(i)) & 1u);  // x + c_i is blocked
         const uint32_t m = nb.at(dir_x(i), dir_y(i), dir_z(i));
-        const float vp = behind ? ph0 : phf[m];
-        const float vr = behind ? rh0 : rhf[m];
+        const float2 v = behind ? fl0 : fl[m];
+        const float vp = v.x, vr = v.y;
         const float w3 = 3.0f * weight(i);
         if (dir_x(i)) { gp[0] += dir_x(i) * w3 * vp; gr[0] += dir_x(i) * w3 * vr; }
         if (dir_y(i)) { gp[1] += dir_y(i) * w3 * vp; gr[1] += dir_y(i) * w3 * vr; }
