@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(CG_BLOCK) k_cg_fields(KParams p, CgArgs q, con
 }
 
 template <bool ODD, bool LINKS>
-__global__ void __launch_bounds__(CG_BLOCK, 3) k_cg_step(KParams p, CgArgs q, float* __restrict__ fr) {
+__global__ void __launch_bounds__(CG_BLOCK, 4) k_cg_step(KParams p, CgArgs q, float* __restrict__ fr) {
     const int x = blockIdx.x * CG_BLOCK + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= p.nx) return;
@@ -198,6 +198,14 @@ __global__ void __launch_bounds__(CG_BLOCK, 3) k_cg_step(KParams p, CgArgs q, fl
     const float pa = g2 > 0.0f ? 0.5f * q.A * gn : 0.0f;
     const float inv_g2 = g2 > 0.0f ? 1.0f / g2 : 0.0f, inv_gn = g2 > 0.0f ? 1.0f / gn : 0.0f;
     const float fr_share = rr / rho, rec = q.beta * rr * rb / rho;  // beta rho_r rho_b / rho^2 * rho
+    // the scatter's neighbour offsets again, from values the compiler cannot tie to the ones above
+    // (so that it does not hold them through the collision: 128 registers, four blocks per SM)
+    uint32_t xs = (uint32_t)x, ys = (uint32_t)y, zs = (uint32_t)z;
+    asm volatile("mov.b32 %0, %0;" : "+r"(xs));
+    asm volatile("mov.b32 %0, %0;" : "+r"(ys));
+    asm volatile("mov.b32 %0, %0;" : "+r"(zs));
+    const Nbr nbs((int)xs, (int)ys, (int)zs, p);
+    const uint32_t selfs = nbs.self();
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         const float cg = dir_x(i) * gp[0] + dir_y(i) * gp[1] + dir_z(i) * gp[2];
@@ -206,8 +214,8 @@ __global__ void __launch_bounds__(CG_BLOCK, 3) k_cg_step(KParams p, CgArgs q, fl
         const float r = fr_share * fs + rec * cosv * phi_w(i, alpha);
         // AA scatter of both colours
         const uint32_t NN = (uint32_t)p.N;
-        uint32_t a = (uint32_t)dir_opp(i) * NN + self;
-        if (ODD && !(LINKS && ((link >> dir_opp(i)) & 1u))) a = (uint32_t)i * NN + nb.at(dir_x(i), dir_y(i), dir_z(i));
+        uint32_t a = (uint32_t)dir_opp(i) * NN + selfs;
+        if (ODD && !(LINKS && ((link >> dir_opp(i)) & 1u))) a = (uint32_t)i * NN + nbs.at(dir_x(i), dir_y(i), dir_z(i));
         fr[a] = r;
         q.fb[a] = fs - r;
     }
