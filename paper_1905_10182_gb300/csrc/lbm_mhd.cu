@@ -135,7 +135,7 @@ struct MhdArgs {
 };
 
 template <bool ODD, bool LINKS>
-__global__ void __launch_bounds__(MHD_BLOCK, 4) k_mhd_step(KParams p, MhdArgs q, float* __restrict__ f) {
+__global__ void __launch_bounds__(MHD_BLOCK, 5) k_mhd_step(KParams p, MhdArgs q, float* __restrict__ f) {
     const int x = blockIdx.x * MHD_BLOCK + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z + p.z0;
     if (x >= p.nx) return;
@@ -153,7 +153,16 @@ __global__ void __launch_bounds__(MHD_BLOCK, 4) k_mhd_step(KParams p, MhdArgs q,
     const float u2 = mc.ux * mc.ux + mc.uy * mc.uy + mc.uz * mc.uz;
     const bool bad = !(mc.rho > 0.0f) || !(u2 < 1.0f);
     if (__any_sync(__activemask(), bad) && bad) atomicOr(p.flag, 1u);
-    aa_scatter<float, ODD, LINKS, true>(f, p.N, nb, link, g);
+    {
+        // the scatter's neighbour offsets again, from values the compiler cannot tie to the ones
+        // above (so that it does not hold them through the collision: 96 registers, 5 blocks per SM)
+        uint32_t xs = (uint32_t)x, ys = (uint32_t)y, zs = (uint32_t)z;
+        asm volatile("mov.b32 %0, %0;" : "+r"(xs));
+        asm volatile("mov.b32 %0, %0;" : "+r"(ys));
+        asm volatile("mov.b32 %0, %0;" : "+r"(zs));
+        const Nbr nbs((int)xs, (int)ys, (int)zs, p);
+        aa_scatter<float, ODD, LINKS, true>(f, p.N, nbs, link, g);
+    }
 }
 
 // rho, u (with (F_ext + F_L)/2), b, j at the current time; out: 10 planes of N (rho, u, b, j).
