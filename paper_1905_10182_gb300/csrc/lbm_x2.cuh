@@ -15,7 +15,7 @@
 
 namespace cmlbm {
 
-constexpr int X2_BLOCK = 128;  // threads per block: 256 nodes of one row
+constexpr int X2_BLOCK = 128;  // threads per block: 128 consecutive node pairs (rows numbered one after another)
 
 // ----------------------------------------------------------------------------- packed pairs
 struct V2 {
