@@ -49,6 +49,18 @@ def random_deviations(nx, ny, nz, seed, amp=1e-3, density=None):
     return g.astype(np.float32)
 
 
+def random_deviations_device(nx, ny, nz, seed, amp=1e-3, device="cuda"):
+    """Population deviations (27, nz, ny, nx) float32, uniform in [-amp, amp], drawn on the device
+    by torch's seeded generator (Philox), for grids too large to build on the host (512^3: 14.5 GB).
+    The numbers differ from random_deviations with the same seed."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    g = torch.empty((27, nz, ny, nx), dtype=torch.float32, device=device)
+    g.uniform_(-amp, amp, generator=gen)
+    return g
+
+
 def random_force_field(nx, ny, nz, seed, amp=1e-4):
     rng = np.random.default_rng(seed + 7919)
     return rng.uniform(-amp, amp, (3, nz, ny, nx)).astype(np.float32)
@@ -74,16 +86,17 @@ def taylor_green(n, u0, rho0=1.0):
     """Standard 3D Taylor-Green vortex on a periodic n^3 box with x = 2 pi i / n:
     u = u0 sin x cos y cos z, v = -u0 cos x sin y cos z, w = 0, and the matching pressure
     p - p0 = rho0 u0^2 / 16 (cos 2x + cos 2y)(cos 2z + 2) turned into density with c_s^2 = 1/3.
-    Returns rho, ux, uy, uz, each (n, n, n) float32 indexed [z, y, x]."""
+    Returns rho, ux, uy, uz, each (n, n, n) float32 indexed [z, y, x].  The factors are
+    separable, so they are formed per axis and broadcast (a 512^3 box needs no FP64 meshgrid)."""
     k = 2.0 * math.pi / n
-    ax = np.arange(n, dtype=np.float64) * k
-    z, y, x = np.meshgrid(ax, ax, ax, indexing="ij")
-    ux = u0 * np.sin(x) * np.cos(y) * np.cos(z)
-    uy = -u0 * np.cos(x) * np.sin(y) * np.cos(z)
-    uz = np.zeros_like(ux)
+    a = np.arange(n, dtype=np.float64) * k
+    x, y, z = a[None, None, :], a[None, :, None], a[:, None, None]
+    ux = (u0 * np.sin(x) * np.cos(y) * np.cos(z)).astype(np.float32)
+    uy = (-u0 * np.cos(x) * np.sin(y) * np.cos(z)).astype(np.float32)
+    uz = np.zeros((n, n, n), dtype=np.float32)
     p = rho0 * u0 * u0 / 16.0 * (np.cos(2 * x) + np.cos(2 * y)) * (np.cos(2 * z) + 2.0)
-    rho = rho0 + 3.0 * p
-    return tuple(a.astype(np.float32) for a in (rho, ux, uy, uz))
+    rho = (rho0 + 3.0 * p).astype(np.float32)
+    return rho, ux, uy, uz
 
 
 def orszag_tang(n, u0=0.0203, b0=0.0203):
@@ -150,11 +163,12 @@ def porous_channel(seed, size_lo=(32, 32, 32), size_hi=(96, 48, 96)):
     return dict(nx=nx, ny=ny, nz=nz, nu=nu, fx=fx, mask=mask, phi_target=phi, seed=seed)
 
 
-def porous_cube(seed, n=64):
+def porous_cube(seed, n=64, nu_range=(0.01, 0.1)):
     """A forced porous channel on an n^3 grid for the learned warm start: walls in y, sphere-pack
-    obstacles (solid fraction target U[0, 0.2]), nu ~ U[0.01, 0.1], F_x ~ U[1e-6, 1e-5]."""
+    obstacles (solid fraction target U[0, 0.2]), nu ~ U[nu_range] (default [0.01, 0.1]),
+    F_x ~ U[1e-6, 1e-5]."""
     rng = SplitMix(2_000_003 + seed)
-    nu = rng.uniform(0.01, 0.1)
+    nu = rng.uniform(*nu_range)
     fx = rng.uniform(1e-6, 1e-5)
     mask, phi = sphere_pack(n, n, n, 7_000_001 + seed)
     return dict(nx=n, ny=n, nz=n, nu=nu, fx=fx, mask=mask, phi_target=phi, seed=seed)

@@ -201,10 +201,10 @@ def test_kolmogorov_1000_steps_fp32(orc):
     assert err <= 1e-6
 
 
-@pytest.mark.parametrize("storage,bound", [("fp16", 5e-3), ("bf16", 0.5)])
+@pytest.mark.parametrize("storage,bound", [("fp16", 1.2e-3), ("bf16", 0.4)])
 def test_kolmogorov_reduced_precision_measured(orc, storage, bound):
-    """FP16/BF16 deviation storage: the measured error after 1000 steps is reported (and kept under
-    a loose sanity bound)."""
+    """FP16/BF16 deviation storage: the error after 1000 steps is reported and held to about twice
+    the measured value (5.7e-4 U0 for FP16, 0.19 U0 for BF16)."""
     N, nu, F0, steps = 32, 0.05, 1e-5, 1000
     s = Solver(N, N, N, nu=nu, storage=storage)
     s.set_force("kolmogorov", (F0,))
@@ -238,27 +238,6 @@ def test_stats_match_oracle_diagnostics(orc):
     assert st["fluid_nodes"] == nx * ny * nz
     assert st["step"] == 3
     assert 0 < st["residual"] < 10
-
-
-def test_full_size_droplet_sampled(orc):
-    """128^3 Shan-Chen droplet (bench launch configuration): one fused step from a seeded state,
-    checked at 3000 sampled nodes the oracle computes one by one."""
-    N = 128
-    rho = inputs.droplet_density(N, radius=24)
-    g = inputs.random_deviations(N, N, N, seed=9, density=rho)
-    s = Solver(N, N, N, nu=1 / 6)
-    s.set_force("shan_chen", (-5.5,))
-    s.set_populations(g)
-    s.step(1)
-    got = s.get_populations().reshape(27, -1)
-    og = orc.Grid(N, N, N, nu=1 / 6, force_kind=orc.FORCE_SHAN_CHEN, G=-5.5)
-    f = full(orc, g)
-    nodes = np.random.default_rng(10).choice(N ** 3, 3000, replace=False)
-    ref = og.step_sampled(f, nodes) - orc.weights()[None, :]
-    S = scale(orc, f, og)
-    err = np.abs(got[:, nodes].T - ref).max()
-    print(f"droplet 128^3 sampled one-step max error {err:.3e} (S = {S:.3e})")
-    assert err <= C_STEP * EPS32 * S, err
 
 
 def test_divergence_is_reported():
@@ -339,6 +318,16 @@ def test_checkpoint_file_resume_bit_exact(tmp_path, storage, odd):
     wrong = Solver(nx + 1, ny, nz, nu=0.03, walls_y=True, storage=storage)
     with pytest.raises(LbmError):
         wrong.load(tmp_path / "ck.bin")
+    # other physics: viscosity, force parameter, force kind, Hermite orders
+    for nu, force, orders in ((0.04, ("kolmogorov", (2e-5,)), None), (0.03, ("kolmogorov", (3e-5,)), None),
+                              (0.03, ("uniform", (2e-5, 0, 0)), None), (0.03, ("kolmogorov", (2e-5,)), (2, 2))):
+        other = Solver(nx, ny, nz, nu=nu, walls_y=True, storage=storage)
+        other.set_force(*force)
+        if orders:
+            other.set_hermite_orders(*orders)
+        with pytest.raises(LbmError):
+            other.load(tmp_path / "ck.bin")
+        assert other.time == 0
 
 
 def _moving_state(orc, nx, ny, nz, seed, umax=0.1, drho=0.1):
