@@ -217,12 +217,15 @@ LBM_API lbm_status lbm_stream_only(lbm_ctx* ctx, int nsteps);
 LBM_API size_t lbm_halo_bytes(const lbm_ctx* ctx);
 LBM_API lbm_status lbm_halo_pack(lbm_ctx* ctx, int face, int stage, void* buf);
 LBM_API lbm_status lbm_halo_unpack(lbm_ctx* ctx, int face, int stage, const void* buf);
-/* Checkpoint / resume.  lbm_save writes a header (grid, storage, boundaries, nu, rho0, force,
- * step counter, AA parity) and the raw population store to path; lbm_load reads it back into a
- * context created with the same grid, storage and boundaries (LBM_ERR_STATE otherwise) and
+/* Checkpoint / resume.  lbm_save writes a header (grid, storage, boundaries, nu, rho0, force
+ * kind and parameters, Hermite orders, step counter, AA parity) and the raw population store to
+ * path.  lbm_load reads it back into a context created and configured like the saved one: the
+ * same grid, storage and boundaries, nu and rho0, force kind and parameters (lbm_set_force) and
+ * Hermite orders (lbm_set_hermite_orders), else LBM_ERR_STATE and the context is unchanged.  It
  * restores the step counter and parity, so that a resumed run continues bit for bit.  Force
  * fields and masks are not saved: set them again on the new context.  Both wait for the stream.
- * A context with a magnetic field (lbm_set_magnetic): LBM_ERR_UNSUPPORTED. */
+ * A context with a magnetic field (lbm_set_magnetic) or a colour-gradient two-phase model
+ * (lbm_set_colour_gradient): LBM_ERR_UNSUPPORTED. */
 LBM_API lbm_status lbm_save(lbm_ctx* ctx, const char* path);
 LBM_API lbm_status lbm_load(lbm_ctx* ctx, const char* path);
 
@@ -237,7 +240,8 @@ LBM_API lbm_status lbm_macroscopic(lbm_ctx* ctx, float* rho, float* ux, float* u
 #define LBM_STATS_LEN 10
 /* FP64 diagnostics over fluid nodes at the current time (host array of LBM_STATS_LEN):
  *   [0] mass sum rho   [1..3] momentum sum rho u   [4] residual |u - u_prev|_2 / |u|_2, u_prev
- *   being u at the previous lbm_stats call (1.0 on the first call)   [5] kinetic energy,
+ *   being u at the previous lbm_stats call (1.0 on the first call; NaN when the fields hold a
+ *   non-finite value)   [5] kinetic energy,
  *   mean of |u|^2/2   [6] enstrophy, mean of |curl u|^2/2 (second-order central differences,
  *   u = 0 behind walls and on solid nodes)   [7] max |u|   [8] fluid node count   [9] step.
  * Deterministic: fixed reduction order.  Waits for the stream. */
@@ -311,7 +315,8 @@ LBM_API lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
 /* Steps the active domains in graph-replayed chunks of check_every (even, >= 2) steps until each
  * reaches residual <= tol (after at least two checks), diverges, or max_steps elapse.  Per domain
  * (arrays of count, optional): steps[k] = steps taken at retirement (or at the end), residual[k]
- * = last residual, status[k] = 0 steady, 1 not steady after max_steps, 2 diverged. */
+ * = last residual, status[k] = 0 steady, 1 not steady after max_steps, 2 diverged (a NaN or
+ * infinite residual: a domain whose fields hold a non-finite value is never reported steady). */
 LBM_API lbm_status lbm_batch_run(lbm_batch* b, double tol, long long max_steps, int check_every, long long* steps,
                                  double* residual, int* status);
 
@@ -338,7 +343,8 @@ LBM_API void lbm_batch_destroy(lbm_batch* b);
  * Element (m, k) of A[b] is at A + b*sab + m*sam + k*sak (BF16 elements), (k, n) of B at
  * B + b*sbb + k*sbk + n*sbn, (m, n) of C at C + b*scb + m*scm + n*scn (FP32, or BF16 with
  * out_bf16).  All pointers are device memory; err is a device flag set to 1 if an internal
- * bounded wait timed out.  Enqueued on stream; LBM_ERR_ARG on bad sizes. */
+ * bounded wait timed out, after which C is undefined (MMAs committed before the timeout may still
+ * be writing it).  Enqueued on stream; LBM_ERR_ARG on bad sizes. */
 LBM_API lbm_status lbm_gemm_bf16(int M, int N, int K, int batch, const void* A, long long sam, long long sak,
                                  long long sab, const void* B, long long sbk, long long sbn, long long sbb, void* C,
                                  long long scm, long long scn, long long scb, int out_bf16, float alpha, int beta,
@@ -371,6 +377,8 @@ LBM_API lbm_status lbm_no_backward(lbm_no* n, const float* dout);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error over all outputs;
  * loss (optional, host) receives the loss before the step.  in, target: device pointers. */
 LBM_API lbm_status lbm_no_train_step(lbm_no* n, int batch, const float* in, const float* target, float lr, double* loss);
+/* A call that returns LBM_ERR_TIMEOUT (a tensor-core wait gave up) leaves the operator's outputs,
+ * gradients, parameters and Adam state undefined: destroy it and create a new one. */
 LBM_API const char* lbm_no_last_error(const lbm_no* n);
 LBM_API void lbm_no_destroy(lbm_no* n);
 

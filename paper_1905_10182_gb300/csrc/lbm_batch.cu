@@ -205,7 +205,12 @@ __global__ void k_batch_residual_final(const int* __restrict__ first, const int*
         a += partials[2ll * t];
         b += partials[2ll * t + 1];
     }
-    res[k] = b > 0.0 ? sqrt(a / b) / window : (a > 0.0 ? INFINITY : 0.0);
+    // a non-finite field (a diverged or NaN-initialised domain) must not read as steady: NaN sums
+    // give a NaN residual, which the host reports as diverged
+    if (!isfinite(a) || !isfinite(b))
+        res[k] = NAN;
+    else
+        res[k] = b > 0.0 ? sqrt(a / b) / window : (a > 0.0 ? INFINITY : 0.0);
 }
 
 // Link words of one domain (as in the single-domain path): bit i = source x - c_i blocked.

@@ -38,6 +38,7 @@ struct lbm_ctx {
     int force_kind = LBM_FORCE_NONE;
     float F[3] = {0, 0, 0};
     float G = 0;
+    double kolm_F0 = 0;  // amplitude of the Kolmogorov force (its table is on the device)
     int eq_order = 6, force_order = 6;  // Hermite truncation orders (6, 6): M1; (6, 2): M4; (2, 2): M5
     float* kolm = nullptr;  // ny entries
     float* field = nullptr; // 3N
@@ -438,6 +439,7 @@ lbm_status lbm_set_force(lbm_ctx* c, int kind, const double* params, const float
         if (!c->kolm) CK(c, cudaMalloc(&c->kolm, sizeof(float) * c->ny), "cudaMalloc(kolmogorov)");
         k_kolmogorov_table<<<(c->ny + 127) / 128, 128, 0, c->stream>>>(c->kolm, c->ny, params[0]);
         CK(c, cudaGetLastError(), "kolmogorov table");
+        c->kolm_F0 = params[0];
         break;
     }
     case LBM_FORCE_FIELD: {
@@ -773,7 +775,8 @@ lbm_status lbm_stats(lbm_ctx* c, double* out) {
     out[1] = s[1];
     out[2] = s[2];
     out[3] = s[3];
-    out[4] = s[5] > 0.0 ? std::sqrt(s[4] / s[5]) : 0.0;
+    // non-finite sums (NaN or inf in the fields) give a NaN residual, never a steady-looking 0
+    out[4] = !(std::isfinite(s[4]) && std::isfinite(s[5])) ? NAN : (s[5] > 0.0 ? std::sqrt(s[4] / s[5]) : 0.0);
     out[5] = cnt > 0 ? 0.5 * s[5] / cnt : 0.0;
     out[6] = cnt > 0 ? s[6] / cnt : 0.0;
     out[7] = std::sqrt(s[7]);
@@ -824,6 +827,14 @@ lbm_status lbm_halo_unpack(lbm_ctx* c, int face, int stage, const void* buf) {
 
 int lbm_parity(const lbm_ctx* c) { return c ? c->parity : -1; }
 
+// Force parameters a checkpoint records: F of a uniform force, (F0, 0, 0) of the Kolmogorov force.
+static void ckpt_force(const lbm_ctx* c, float out[3]) {
+    const bool kolm = c->force_kind == LBM_FORCE_KOLMOGOROV;
+    out[0] = kolm ? (float)c->kolm_F0 : c->F[0];
+    out[1] = kolm ? 0.0f : c->F[1];
+    out[2] = kolm ? 0.0f : c->F[2];
+}
+
 // Checkpoint file: a fixed header, then the raw population store (storage type, AA order as is).
 struct CkptHeader {
     char magic[8];
@@ -855,7 +866,7 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
     h.force_kind = c->force_kind;
     h.eq_order = c->eq_order;
     h.force_order = c->force_order;
-    std::memcpy(h.F, c->F, sizeof(h.F));
+    ckpt_force(c, h.F);
     h.G = c->G;
     h.store_bytes = (uint64_t)27 * (uint64_t)c->N * elem_size(c->storage);
     std::vector<char> buf(h.store_bytes);
@@ -880,6 +891,20 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
                h.walls_y != c->walls_y || h.store_bytes != (uint64_t)27 * (uint64_t)c->N * elem_size(c->storage))) {
         std::fclose(fp);
         return fail(c, LBM_ERR_STATE, "checkpoint grid, storage or boundaries differ from the context");
+    }
+    // the physics must be the one the store was advanced with, else the resume would not continue
+    // the checkpointed run (the force field and the mask are not in the file: the caller sets them)
+    float Fc[3];
+    ckpt_force(c, Fc);
+    if (ok && (h.nu != c->nu || h.rho0 != c->rho0 || h.force_kind != c->force_kind || h.G != c->G ||
+               std::memcmp(h.F, Fc, sizeof(h.F)) != 0 || h.eq_order != c->eq_order ||
+               h.force_order != c->force_order)) {
+        std::fclose(fp);
+        return fail(c, LBM_ERR_STATE, "checkpoint nu, rho0, force or Hermite orders differ from the context");
+    }
+    if (ok && (h.parity != 0 && h.parity != 1)) {
+        std::fclose(fp);
+        return fail(c, LBM_ERR_STATE, "checkpoint header holds an invalid AA parity");
     }
     std::vector<char> buf(ok ? h.store_bytes : 0);
     if (ok) ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();

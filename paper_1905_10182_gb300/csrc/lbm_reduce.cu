@@ -239,7 +239,8 @@ __global__ void k_noalloc_derive(const double* __restrict__ t, double* __restric
     out[1] = t[1];
     out[2] = t[2];
     out[3] = t[3];
-    out[4] = t[5] > 0.0 ? sqrt(t[4] / t[5]) : 0.0;
+    // non-finite sums (NaN or inf in the fields) give a NaN residual, never a steady-looking 0
+    out[4] = !(isfinite(t[4]) && isfinite(t[5])) ? NAN : (t[5] > 0.0 ? sqrt(t[4] / t[5]) : 0.0);
     out[5] = cnt > 0.0 ? 0.5 * t[5] / cnt : 0.0;
     out[6] = cnt > 0.0 ? t[6] / cnt : 0.0;
     out[7] = sqrt(t[7]);
