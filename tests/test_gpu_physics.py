@@ -1,9 +1,10 @@
 """Physics of the benchmark configurations on the GPU path (through the C ABI).
 
-* Four-rolls mill (Sec. III A, run in 2D with nz = 1): second-order convergence to the closed form;
-  the paper reports a rate of 1.998 (tests/golden/four_rolls_mill.txt).
+* Four-rolls mill (Sec. III A, run in 2D with nz = 1): the paper's convergence study, N = 8 .. 256 at
+  u0 = 1e-3 and 1e-2, second order against the closed form (the paper reports a rate of 1.998,
+  tests/golden/four_rolls_mill.txt); one step of the same 2D field-force case against the oracle.
 * Static droplet with the Shan-Chen force (Sec. III, static droplet): Laplace's law dp = 2 sigma / R
-  at 128^3 for R = 16, 24, 32, and the same surface tension from the FP64 oracle at 32^3.
+  at 128^3 for R = 16, 24, 32, and the surface tension against the FP64 oracle's at 64^3.
 * Decaying Taylor-Green vortex: the kinetic-energy decay rate equals -2 nu x enstrophy (energy
   equation of periodic incompressible flow), both taken from the FP64 diagnostics of lbm_stats;
   and at low viscosity (nu = 1e-4, 64^3, 5000 steps through the transition) the GPU's kinetic-energy
@@ -20,12 +21,15 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+from droplet_laplace import surface_tension  # noqa: E402
 from golden_util import load_table  # noqa: E402
 from paper_1905_10182_gb300 import Solver, inputs  # noqa: E402
 
 
-def _four_rolls_error(N, u0=1e-3, Re=100.0):
-    nu = u0 * N / Re
+def _four_rolls_fields(N, u0):
+    """Force field and steady closed form (Eq. tg_vel) of the four-rolls mill on an N x N x 1 grid,
+    nu from Re = u0 N / nu = 100."""
+    nu = u0 * N / 100.0
     psi = 2 * math.pi / N
     x = np.arange(N)
     X, Y = np.meshgrid(x, x, indexing="xy")  # [y][x]
@@ -33,6 +37,13 @@ def _four_rolls_error(N, u0=1e-3, Re=100.0):
     Fy = 2 * nu * u0 * psi ** 2 * np.cos(psi * X) * np.cos(psi * Y)
     ux_an = u0 * np.sin(psi * X) * np.sin(psi * Y)
     uy_an = u0 * np.cos(psi * X) * np.cos(psi * Y)
+    return nu, psi, Fx, Fy, ux_an, uy_an
+
+
+def _four_rolls_error(N, u0=1e-3):
+    """Relative L2 error (Eq. error) of the steady GPU field against Eq. tg_vel.  The run starts
+    from f^eq of the closed form and takes 12 e-folding times of the slowest transient."""
+    nu, psi, Fx, Fy, ux_an, uy_an = _four_rolls_fields(N, u0)
     s = Solver(N, N, 1, nu=nu)
     z = np.zeros((1, N, N), np.float32)
     s.set_force("field", None, Fx[None].astype(np.float32), Fy[None].astype(np.float32), z)
@@ -40,57 +51,87 @@ def _four_rolls_error(N, u0=1e-3, Re=100.0):
     lam = 2 * nu * psi ** 2  # decay rate of the slowest transient
     s.step(int(12.0 / lam))
     _, ux, uy, _ = s.macroscopic()
+    s.close()
     num = np.concatenate([ux[0].ravel(), uy[0].ravel()]).astype(np.float64)
     an = np.concatenate([ux_an.ravel(), uy_an.ravel()])
     return np.linalg.norm(num - an) / np.linalg.norm(an)
 
 
-def test_four_rolls_mill_second_order():
+FOUR_ROLLS_N = (8, 16, 32, 64, 128, 256)
+
+
+@pytest.mark.parametrize("u0", [1e-3, 1e-2])
+def test_four_rolls_mill_second_order(u0):
+    """The convergence study of Sec. III A: N = 8 .. 256 at Re = 100, u0 = 1e-3 and 1e-2.  The
+    least-squares rate over all N is within 0.05 of the paper's 1.998, and every pairwise rate
+    within 0.15 of 2 (the paper: M1 keeps a rate of about 2 for each N at both velocities)."""
     paper_rate = float(load_table("four_rolls_mill.txt")["rate"])
-    errs = [_four_rolls_error(N) for N in (16, 32, 64)]
-    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
-    print(f"four-rolls mill errors {errs}, rates {rates} (paper: {paper_rate})")
-    assert all(abs(r - paper_rate) < 0.1 for r in rates), (errs, rates)
+    errs = np.array([_four_rolls_error(N, u0) for N in FOUR_ROLLS_N])
+    rates = np.log2(errs[:-1] / errs[1:])
+    slope = -np.polyfit(np.log2(FOUR_ROLLS_N), np.log2(errs), 1)[0]
+    print(f"four-rolls mill u0={u0}: errors {errs.tolist()}, pairwise rates {rates.round(4).tolist()}, "
+          f"least-squares rate {slope:.4f} (paper: {paper_rate})")
+    assert abs(slope - paper_rate) < 0.05, (errs, slope)
+    assert np.all(np.abs(rates - 2.0) < 0.15), (errs, rates)
 
 
-def _laplace(rho, G, n):
-    """dp between centre and far corner (p = rho/3 + G psi^2/6) and the volume-equivalent radius."""
-    psi = 1.0 - np.exp(-rho.astype(np.float64))
-    p = rho / 3.0 + G * psi ** 2 / 6.0
-    c = n // 2
-    rl, rg = float(rho[c, c, c]), float(rho[0, 0, 0])
-    dp = float(p[c, c, c] - p[0, 0, 0])
-    V = (rho.astype(np.float64).sum() - rg * n ** 3) / (rl - rg)
-    return dp, (3 * V / (4 * math.pi)) ** (1.0 / 3.0)
+def test_four_rolls_mill_one_step_matches_oracle(orc):
+    """One step of the 2D (nz = 1) field-force case against the oracle, from f^eq of the closed
+    form plus seeded deviations: the grid and force the convergence study runs."""
+    N, u0 = 24, 1e-2
+    nu, _, Fx, Fy, ux_an, uy_an = _four_rolls_fields(N, u0)
+    F = np.stack([Fx, Fy, np.zeros_like(Fx)])[:, None].astype(np.float32)  # (3, 1, N, N)
+    u = np.stack([ux_an, uy_an, np.zeros_like(ux_an)])[:, None]
+    og = orc.Grid(N, N, 1, nu=nu, collision=orc.COLL_PAPER, force_kind=orc.FORCE_FIELD, field=F.astype(np.float64))
+    w = orc.weights()[:, None, None, None]
+    g = (og.init_equilibrium(1.0, u) - w + inputs.random_deviations(N, N, 1, seed=77, amp=1e-4)).astype(np.float32)
+    s = Solver(N, N, 1, nu=nu)
+    s.set_force("field", None, F[0], F[1], F[2])
+    s.set_populations(g)
+    f0 = g.astype(np.float64) + w
+    S = max(np.abs(g).max(), u0, np.abs(F).max())
+    for n in (1, 2):
+        s.step(1)
+        ref = og.step(f0, n) - w
+        err = np.abs(s.get_populations().astype(np.float64) - ref).max()
+        assert err <= n * 64 * 2.0 ** -24 * S, (n, err)
+    s.close()
 
 
-def test_droplet_laplace_law_and_oracle_surface_tension(orc):
-    G, n = -5.5, 128
-    sig = []
-    for R in (16, 24, 32):
-        s = Solver(n, n, n, nu=1 / 6)
-        s.set_force("shan_chen", (G,))
-        z = np.zeros((n, n, n), np.float32)
-        s.set_state(inputs.droplet_density(n, R), z, z, z)
-        s.step(20000)
-        rho, *_ = s.macroscopic()
-        dp, Reff = _laplace(rho, G, n)
-        sig.append(dp * Reff / 2.0)
-    sig = np.array(sig)
-    print(f"GPU 128^3 surface tension per radius: {sig}")
+def _gpu_sigma(n, R, G=-5.5, steps=20000):
+    s = Solver(n, n, n, nu=1 / 6)
+    s.set_force("shan_chen", (G,))
+    z = np.zeros((n, n, n), np.float32)
+    s.set_state(inputs.droplet_density(n, R), z, z, z)
+    s.step(steps)
+    rho, *_ = s.macroscopic()
+    s.close()
+    return surface_tension(rho, G, n)
+
+
+def test_droplet_laplace_law_and_oracle_surface_tension():
+    """Laplace's law on the GPU at 128^3 (R = 16, 24, 32, 20000 steps: dp R constant), and the
+    surface tension against the FP64 oracle at 64^3 (R = 8, 12, 16; stored by
+    tests/golden/make_droplet_sigma.py after 5000 steps, with the 3000-step values showing it has
+    settled).  On the same 64^3 runs the GPU agrees with the oracle to 5e-5 relative per radius
+    (measured 1.1e-5 to 1.2e-5: FP32 storage against FP64, the same scheme).  Across resolutions
+    the measured sigma rises with R at both sizes (the interface keeps its width of about two
+    nodes while the curvature falls: 64^3 R = 8..16 gives 0.0595..0.0605, 128^3 R = 16..32 gives
+    0.0614..0.0619), so the 128^3 mean lies 2.6 % above the 64^3 mean; the bound is 5 %."""
+    G = -5.5
+    gold = load_table("droplet_sigma_oracle64.txt")
+    so = np.array([float(gold[f"sigma_R{R}_s5000"]) for R in (8, 12, 16)])
+    so3 = np.array([float(gold[f"sigma_R{R}_s3000"]) for R in (8, 12, 16)])
+    assert np.all(np.abs(so - so3) <= 1e-3 * np.abs(so)), (so, so3)
+    g64 = np.array([_gpu_sigma(64, R, G, 5000) for R in (8, 12, 16)])
+    d64 = np.abs(g64 - so) / np.abs(so)
+    sig = np.array([_gpu_sigma(128, R, G) for R in (16, 24, 32)])
+    d128 = abs(sig.mean() - so.mean()) / so.mean()
+    print(f"surface tension: GPU 128^3 {sig}, GPU 64^3 {g64}, oracle 64^3 {so}; "
+          f"GPU 64^3 vs oracle per radius {d64}, GPU 128^3 mean vs oracle 64^3 mean {d128:.3e}")
     assert sig.std() / sig.mean() < 0.05  # dp R constant: Laplace's law
-    # the FP64 oracle at 32^3 (R = 6, 8, 10)
-    m = 32
-    so = []
-    for R in (6, 8, 10):
-        g = orc.Grid(m, m, m, nu=1 / 6, force_kind=orc.FORCE_SHAN_CHEN, G=G, collision=orc.COLL_PAPER)
-        f = g.init_equilibrium(inputs.droplet_density(m, R).astype(np.float64), np.zeros((3, m, m, m)))
-        rho, _ = g.macroscopic(g.step(f, 4000))
-        dp, Reff = _laplace(rho, G, m)
-        so.append(dp * Reff / 2.0)
-    so = np.array(so)
-    print(f"oracle 32^3 surface tension per radius: {so}")
-    assert abs(sig.mean() - so.mean()) / so.mean() < 0.15
+    assert np.all(d64 <= 5e-5), d64
+    assert d128 <= 0.05, d128
 
 
 def test_taylor_green_energy_decay_rate():
