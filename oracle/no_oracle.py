@@ -38,28 +38,51 @@ def unpack(theta, D, W, m, L, Ci, Co):
     return {k: theta[o:o + int(np.prod(s))].reshape(s) for k, (o, s) in lay.items()}
 
 
-def spectral_conv(h, Wm, D, m):
-    """h: [B, W, D, D, D] (z, y, x); Wm: [m(kx), 2m(ky), 2m(kz), W(o), W(c), 2]."""
-    Wc = torch.complex(Wm[..., 0], Wm[..., 1])
+def spectral_modes(h, D, m):
+    """Kept Fourier coefficients of h [B, C, D, D, D] (z, y, x): rfftn without scaling, kz, ky in
+    kept(D, m), kx < m; returns [B, C, 2m(kz), 2m(ky), m(kx)] complex."""
     X = torch.fft.rfftn(h, dim=(2, 3, 4))                      # [B, C, kz, ky, kx]
     idx = torch.tensor(kept(D, m))
-    Xk = X[:, :, idx][:, :, :, idx][..., :m]                   # [B, C, 2m, 2m, m]
-    Y = torch.einsum("xyzoc,bczyx->bozyx", Wc, Xk)
-    Yf = torch.zeros(X.shape, dtype=X.dtype)
+    return X[:, :, idx][:, :, :, idx][..., :m]
+
+
+def spectral_mix(Xk, Wm):
+    """Y[b, o, mode] = sum_c W[mode][o][c] X[b, c, mode]; Wm: [m(kx), 2m(ky), 2m(kz), W(o), W(c), 2]."""
+    Wc = torch.complex(Wm[..., 0], Wm[..., 1])
+    return torch.einsum("xyzoc,bczyx->bozyx", Wc, Xk)
+
+
+def spectral_synthesis(Y, D, m):
+    """irfftn (1/D^3) of the kept modes Y [B, O, 2m, 2m, m], every other mode zero."""
+    B, O = Y.shape[:2]
+    idx = torch.tensor(kept(D, m))
+    Yf = torch.zeros((B, O, D, D, D // 2 + 1), dtype=Y.dtype)
     zz, yy = torch.meshgrid(idx, idx, indexing="ij")
     Yf[:, :, zz, yy, :m] = Y
     return torch.fft.irfftn(Yf, s=(D, D, D), dim=(2, 3, 4))
 
 
-def forward(theta, a, D, W, m, L, Ci, Co):
-    """theta: flat float64 tensor; a: [B, Ci, D, D, D] float64 -> [B, Co, D, D, D]."""
+def spectral_conv(h, Wm, D, m):
+    """h: [B, W, D, D, D] (z, y, x); Wm: [m(kx), 2m(ky), 2m(kz), W(o), W(c), 2]."""
+    return spectral_synthesis(spectral_mix(spectral_modes(h, D, m), Wm), D, m)
+
+
+def forward(theta, a, D, W, m, L, Ci, Co, record=None):
+    """theta: flat float64 tensor; a: [B, Ci, D, D, D] float64 -> [B, Co, D, D, D].
+    record: optional dict that receives the intermediates h0 .. h_L (block inputs, h_L the last
+    block's output), X_l (kept modes of h_l), Y_l (mixed modes) and z_l (pre-activations)."""
     pr = unpack(theta, D, W, m, L, Ci, Co)
-    B = a.shape[0]
     h = torch.einsum("ci,bizyx->bczyx", pr["P"], a) + pr["p"][None, :, None, None, None]
     for l in range(L):
-        s = spectral_conv(h, pr[f"Wm{l}"], D, m)
+        Xk = spectral_modes(h, D, m)
+        Y = spectral_mix(Xk, pr[f"Wm{l}"])
+        s = spectral_synthesis(Y, D, m)
         z = s + torch.einsum("oc,bczyx->bozyx", pr[f"Wc{l}"], h) + pr[f"b{l}"][None, :, None, None, None]
+        if record is not None:
+            record.update({f"h{l}": h, f"X{l}": Xk, f"Y{l}": Y, f"z{l}": z})
         h = torch.nn.functional.gelu(z) if l < L - 1 else z
+    if record is not None:
+        record[f"h{L}"] = h
     return torch.einsum("oc,bczyx->bozyx", pr["Q"], h) + pr["q"][None, :, None, None, None]
 
 

@@ -107,6 +107,47 @@ __global__ void k_act_bwd(const float* __restrict__ dh, const float* __restrict_
     }
 }
 
+// Per sample and channel (one block each, S values): the mean m of v = act(src) (FP64 sum, fixed
+// order) and out = bf16(v - m).  The spectral transforms take the centred field: a channel's mean
+// lives in mode (0, 0, 0) only, and the BF16 partial sums over x and y would otherwise carry it
+// into the z transform, where the modes (0, 0, kz != 0) are small differences of large rounded
+// numbers.  The mean's mode is added back in FP32 (k_add_dc).
+__global__ void __launch_bounds__(1024) k_center(const float* __restrict__ src, long long S, int use_gelu,
+                                                 bf16* __restrict__ out, float* __restrict__ mean) {
+    __shared__ double sh[32];
+    __shared__ float m_sh;
+    const long long base = (long long)blockIdx.x * S;
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < S; i += blockDim.x) {
+        const float v = src[base + i];
+        acc += use_gelu ? gelu(v) : v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        m_sh = (float)(t / (double)S);
+        mean[blockIdx.x] = m_sh;
+    }
+    __syncthreads();
+    const float m = m_sh;
+    for (long long i = threadIdx.x; i < S; i += blockDim.x) {
+        const float v = src[base + i];
+        out[base + i] = __float2bfloat16((use_gelu ? gelu(v) : v) - m);
+    }
+}
+
+// Mode (0, 0, 0), real part, of each (sample, channel) row block of a mode array laid out
+// [b][c][kx][ky][ri][kz]: += scale * mean[b * W + c].
+__global__ void k_add_dc(float* __restrict__ modes, const float* __restrict__ mean, int rows, long long stride,
+                         float scale) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < rows) modes[(long long)k * stride] += scale * mean[k];
+}
+
 // Generic 6-axis permutation of a BF16 tensor: out axis j is in axis perm[j].
 struct Perm6 {
     long long din[6];
@@ -318,6 +359,8 @@ struct lbm_no {
     // work buffers
     bf16 *t1 = nullptr, *t2 = nullptr, *t2p = nullptr, *yh = nullptr, *u1 = nullptr, *u1p = nullptr, *u2 = nullptr;
     float* dyh = nullptr;
+    bf16* hs = nullptr;       // centred BF16 input of the spectral transforms [B][W][S]
+    float* hmean = nullptr;   // its per-(sample, channel) means [B][W]
     float *dh = nullptr, *dh2 = nullptr, *dz = nullptr;
     bf16* dzb = nullptr;
     float* part = nullptr;  // split-K partials of the 1x1 weight gradient
@@ -449,14 +492,16 @@ lbm_status upload_dft(lbm_no* n) {
     return LBM_OK;
 }
 
-// spectral convolution of layer l: input hb (BF16 [B][W][S]) -> out (FP32 [B][W][S], overwritten);
-// keeps the mode coefficients in Xh[l] for the weight gradient
-lbm_status spectral_fwd(lbm_no* n, int l, const bf16* hb, float* out) {
+// spectral convolution of layer l: input h = act(src) (FP32 [B][W][S], act = GELU if use_gelu) ->
+// out (FP32 [B][W][S], overwritten); keeps the mode coefficients in Xh[l] for the weight gradient
+lbm_status spectral_fwd(lbm_no* n, int l, const float* src, int use_gelu, float* out) {
     const int B = n->B, W = n->W, D = n->D, MX = n->MX, MY = n->MY, MZ = n->MZ;
     const long long D2 = (long long)D * D;
     const long long BWD = (long long)B * W * D;
+    k_center<<<B * W, 1024, 0, n->stream>>>(src, n->S, use_gelu, n->hs, n->hmean);
+    NCK(n, cudaGetLastError(), "centre");
     // x: [bcz][y][x] x FX -> t1 [bcz][(kx,ri)][y]
-    NCK(n, gemm(n, D, 2 * MX, D, (int)BWD, hb, D, 1, D2, n->FX, 2 * MX, 1, 0, n->t1, 1, D, 2LL * MX * D, 1, 0), "fx");
+    NCK(n, gemm(n, D, 2 * MX, D, (int)BWD, n->hs, D, 1, D2, n->FX, 2 * MX, 1, 0, n->t1, 1, D, 2LL * MX * D, 1, 0), "fx");
     // y: rows (bcz,kx), K = (ri,y) -> t2 [b][c][z][kx][ri][ky]
     NCK(n, gemm(n, (int)(BWD * MX), 2 * MY, 2 * D, 1, n->t1, 2 * D, 1, 0, n->GY, 2 * MY, 1, 0, n->t2, 2 * MY, 1, 0, 1, 0), "fy");
     {
@@ -467,6 +512,10 @@ lbm_status spectral_fwd(lbm_no* n, int l, const bf16* hb, float* out) {
     // z: rows (b,c,kx,ky), K = (ri,z) -> Xh [b][c][kx][ky][ri][kz] FP32
     const long long R = (long long)B * W * MX * MY;
     NCK(n, gemm(n, (int)R, 2 * MZ, 2 * D, 1, n->t2p, 2 * D, 1, 0, n->GZ, 2 * MZ, 1, 0, n->Xh[l], 2 * MZ, 1, 0, 0, 0), "fz");
+    // the mean's mode: sum over the grid = S * mean
+    k_add_dc<<<(B * W + 127) / 128, 128, 0, n->stream>>>(n->Xh[l], n->hmean, B * W, (long long)MX * MY * 2 * MZ,
+                                                         (float)n->S);
+    NCK(n, cudaGetLastError(), "dc mode");
     MixDims md{B, W, MX, MY, MZ};
     k_mix_fwd<<<grid_for((long long)B * W * MX * MY * MZ), 256, 0, n->stream>>>(n->Xh[l], n->params + n->oWm[l], md, n->yh);
     NCK(n, cudaGetLastError(), "mix");
@@ -486,13 +535,16 @@ lbm_status spectral_fwd(lbm_no* n, int l, const bf16* hb, float* out) {
 
 // adjoint of the spectral convolution of layer l: dzb (BF16 gradient of its output) -> dh
 // (FP32, accumulated); adds the mixing-weight gradient
-lbm_status spectral_bwd(lbm_no* n, int l, const bf16* dzb, float* dh) {
+lbm_status spectral_bwd(lbm_no* n, int l, const float* dz, float* dh) {
     const int B = n->B, W = n->W, D = n->D, MX = n->MX, MY = n->MY, MZ = n->MZ;
     const long long D2 = (long long)D * D;
     const long long BWD = (long long)B * W * D;
     const long long R = (long long)B * W * MX * MY;
+    // the adjoint transforms take the centred gradient too (see k_center)
+    k_center<<<B * W, 1024, 0, n->stream>>>(dz, n->S, 0, n->hs, n->hmean);
+    NCK(n, cudaGetLastError(), "centre");
     // adjoint of inverse x -> u2 layout
-    NCK(n, gemm(n, D, 2 * MX, D, (int)BWD, dzb, D, 1, D2, n->HX, 1, D, 0, n->u2, 1, D, 2LL * MX * D, 1, 0), "ix^T");
+    NCK(n, gemm(n, D, 2 * MX, D, (int)BWD, n->hs, D, 1, D2, n->HX, 1, D, 0, n->u2, 1, D, 2LL * MX * D, 1, 0), "ix^T");
     // adjoint of inverse y -> u1p layout
     NCK(n, gemm(n, (int)(BWD * MX), 2 * MY, 2 * D, 1, n->u2, 2 * D, 1, 0, n->HY, 1, 2 * D, 0, n->u1p, 2 * MY, 1, 0, 1, 0),
         "iy^T");
@@ -503,6 +555,9 @@ lbm_status spectral_bwd(lbm_no* n, int l, const bf16* dzb, float* dh) {
     }
     // adjoint of inverse z -> dYh (FP32)
     NCK(n, gemm(n, (int)R, 2 * MZ, 2 * D, 1, n->u1, 2 * D, 1, 0, n->HZ, 1, 2 * D, 0, n->dyh, 2 * MZ, 1, 0, 0, 0), "iz^T");
+    // the mean's mode: the adjoint of the inverse's 1/D^3 sum over the grid = the mean
+    k_add_dc<<<(B * W + 127) / 128, 128, 0, n->stream>>>(n->dyh, n->hmean, B * W, (long long)MX * MY * 2 * MZ, 1.0f);
+    NCK(n, cudaGetLastError(), "dc mode");
     MixDims md{B, W, MX, MY, MZ};
     k_mix_bwd_w<<<grid_for((long long)MX * MY * MZ * W * W), 256, 0, n->stream>>>(n->dyh, n->Xh[l], md,
                                                                                    n->grads + n->oWm[l]);
@@ -542,7 +597,7 @@ lbm_status forward(lbm_no* n, int B, const float* in, float* out) {
     for (int l = 0; l < n->L; ++l) {
         k_f32_to_bf16<<<grid_for((long long)W * W), 256, 0, n->stream>>>(n->params + n->oWc[l], n->wcb + (long long)l * W * W,
                                                                            (long long)W * W);
-        st = spectral_fwd(n, l, n->hb[l], n->z[l]);
+        st = l == 0 ? spectral_fwd(n, l, n->h0, 0, n->z[l]) : spectral_fwd(n, l, n->z[l - 1], 1, n->z[l]);
         if (st) return st;
         // 1x1 conv accumulated onto the spectral output: z[b][o][s] += sum_c Wc[o][c] h[b][c][s]
         NCK(n, gemm(n, (int)S, W, W, B, n->hb[l], 1, S, (long long)W * S, n->wcb + (long long)l * W * W, 1, W, 0, n->z[l], 1,
@@ -596,7 +651,7 @@ lbm_status backward(lbm_no* n, const float* dout) {
         NCK(n, gemm(n, (int)S, W, W, B, n->dzb, 1, S, (long long)W * S, n->wcb + (long long)l * W * W, W, 1, 0, n->dh2, 1, S,
                     (long long)W * S, 0, 0),
             "conv dX");
-        lbm_status st = spectral_bwd(n, l, n->dzb, n->dh2);
+        lbm_status st = spectral_bwd(n, l, n->dz, n->dh2);
         if (st) return st;
         std::swap(n->dh, n->dh2);
     }
@@ -611,7 +666,7 @@ lbm_status check_gemm(lbm_no* n) {
     unsigned int e = 0;
     NCK(n, cudaMemcpyAsync(&e, n->gemm_err, sizeof(e), cudaMemcpyDeviceToHost, n->stream), "gemm flag");
     NCK(n, cudaStreamSynchronize(n->stream), "sync");
-    if (e) return nfail(n, LBM_ERR_TIMEOUT, "a tensor-core GEMM wait timed out");
+    if (e) return nfail(n, LBM_ERR_TIMEOUT, "a tensor-core GEMM wait timed out: outputs, gradients and parameters of this operator are undefined; destroy it");
     return LBM_OK;
 }
 
@@ -710,6 +765,8 @@ lbm_status lbm_no_create(int D, int W, int modes, int L, int Ci, int Co, int max
     alloc((void**)&n->dh2, sizeof(float) * act);
     alloc((void**)&n->dz, sizeof(float) * act);
     alloc((void**)&n->dzb, sizeof(bf16) * act);
+    alloc((void**)&n->hs, sizeof(bf16) * act);
+    alloc((void**)&n->hmean, sizeof(float) * maxB * W);
     alloc((void**)&n->part, sizeof(float) * maxB * ((S + KSPLIT - 1) / KSPLIT + 1) * W * W);
     alloc((void**)&n->dout, sizeof(float) * maxB * Co * S);
     alloc((void**)&n->loss_d, sizeof(double));
@@ -787,7 +844,7 @@ void lbm_no_destroy(lbm_no* n) {
     if (!n) return;
     cudaStreamSynchronize(n->stream);
     void* bufs[] = {n->params, n->grads, n->adam_m, n->adam_v, n->wcb, n->a_in, n->h0, n->FX, n->GY, n->GZ, n->HZ, n->HY,
-                    n->HX, n->t1, n->t2, n->t2p, n->yh, n->dyh, n->u1, n->u1p, n->u2, n->dh, n->dh2, n->dz, n->dzb,
+                    n->HX, n->t1, n->t2, n->t2p, n->yh, n->dyh, n->u1, n->u1p, n->u2, n->dh, n->dh2, n->dz, n->dzb, n->hs, n->hmean,
                     n->part, n->dout, n->loss_d, n->gemm_err};
     for (void* b : bufs) cudaFree(b);
     for (bf16* b : n->hb) cudaFree(b);

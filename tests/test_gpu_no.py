@@ -14,20 +14,24 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from oracle import no_oracle as no  # noqa: E402
 from paper_1905_10182_gb300.neural import NeuralOperator  # noqa: E402
+from no_params import host_params  # noqa: E402
 
 CFG = dict(D=16, W=8, m=4, L=2, Ci=4, Co=4)
 
 
 def _model(seed=3, B=2):
+    """The operator with seeded host-side parameters (also returned, as float64, for the oracle)."""
     c = CFG
-    return NeuralOperator(D=c["D"], width=c["W"], modes=c["m"], layers=c["L"], in_ch=c["Ci"], out_ch=c["Co"],
-                          max_batch=B, seed=seed)
+    net = NeuralOperator(D=c["D"], width=c["W"], modes=c["m"], layers=c["L"], in_ch=c["Ci"], out_ch=c["Co"],
+                         max_batch=B, seed=seed)
+    theta = host_params(no.layout(c["D"], c["W"], c["m"], c["L"], c["Ci"], c["Co"]), c["W"], seed)
+    net.set_params(theta)
+    return net, theta.astype(np.float64)
 
 
 def test_forward_matches_oracle():
     c = CFG
-    net = _model()
-    theta = net.get_params().astype(np.float64)
+    net, theta = _model()
     rng = np.random.default_rng(4)
     a = rng.normal(size=(2, c["Ci"], c["D"], c["D"], c["D"])).astype(np.float32)
     out = torch.empty((2, c["Co"], c["D"], c["D"], c["D"]), device="cuda")
@@ -40,8 +44,7 @@ def test_forward_matches_oracle():
 
 def test_gradients_match_oracle():
     c = CFG
-    net = _model(seed=5)
-    theta = net.get_params().astype(np.float64)
+    net, theta = _model(seed=5)
     rng = np.random.default_rng(6)
     a = rng.normal(size=(2, c["Ci"], c["D"], c["D"], c["D"])).astype(np.float32)
     dout = rng.normal(size=(2, c["Co"], c["D"], c["D"], c["D"])).astype(np.float32)
@@ -61,7 +64,7 @@ def test_gradients_match_oracle():
 
 def test_training_reduces_loss():
     c = CFG
-    net = _model(seed=7, B=2)
+    net, _ = _model(seed=7, B=2)
     rng = np.random.default_rng(8)
     D = c["D"]
     a = rng.normal(size=(2, c["Ci"], D, D, D)).astype(np.float32)
