@@ -6,7 +6,7 @@ modes, batch 4: memory-bound, GB/s of A + B read and C written against the HBM c
 the time of one training step (forward, backward, Adam) of that operator.  CUDA events on the
 launching stream, after warm-up.
 
-    python -m paper_1905_10182_gb300.gemm_bench
+    python -m paper_1905_10182_gb300.gemm_bench [--profile-shapes]
 """
 from __future__ import annotations
 
@@ -60,9 +60,25 @@ def time_gemm(M, N, K, batch, sa, sb, sc, reps=20):
     return e0.elapsed_time(e1) / reps
 
 
+def profile_shapes():
+    """One timed launch (after 3 warm-ups) of the square, x-DFT and 1x1-map products, in that order:
+    launches 3, 7 and 11 of k_gemm_bf16_tc, for an ncu capture."""
+    n = 8192
+    D, W, MX, B = 64, 32, 12, 4
+    S, BWD = D ** 3, B * W * D
+    time_gemm(n, n, n, 1, (n, 1, 0), (n, 1, 0), (n, 1, 0), reps=1)
+    time_gemm(D, 2 * MX, D, BWD, (D, 1, D * D), (2 * MX, 1, 0), (1, D, 2 * MX * D), reps=1)
+    time_gemm(S, W, W, B, (1, S, W * S), (1, W, 0), (1, S, W * S), reps=1)
+
+
 def main():
+    import sys
+
     import torch
     torch.cuda.set_device(0)
+    if "--profile-shapes" in sys.argv:
+        profile_shapes()
+        return
     tf_peak, gb_peak, src = _peaks()
     n = 8192
     ms = time_gemm(n, n, n, 1, (n, 1, 0), (n, 1, 0), (n, 1, 0), reps=5)
