@@ -6,7 +6,7 @@ modes, batch 4: memory-bound, GB/s of A + B read and C written against the HBM c
 the time of one training step (forward, backward, Adam) of that operator.  CUDA events on the
 launching stream, after warm-up.
 
-    python -m paper_1905_10182_gb300.gemm_bench [--profile-shapes]
+    python -m paper_1905_10182_gb300.gemm_bench [--profile-shapes | --train-step]
 """
 from __future__ import annotations
 
@@ -79,6 +79,9 @@ def main():
     if "--profile-shapes" in sys.argv:
         profile_shapes()
         return
+    if "--train-step" in sys.argv:
+        print(json.dumps(train_step_time()), flush=True)
+        return
     tf_peak, gb_peak, src = _peaks()
     n = 8192
     ms = time_gemm(n, n, n, 1, (n, 1, 0), (n, 1, 0), (n, 1, 0), reps=5)
@@ -104,8 +107,16 @@ def main():
                           "gbs": byts / (ms * 1e-3) / 1e9, "peak_gbs": gb_peak,
                           "frac_hbm": byts / (ms * 1e-3) / 1e9 / gb_peak,
                           "tflops": flops / (ms * 1e-3) / 1e12}), flush=True)
-    # one training step of the operator
+    print(json.dumps(train_step_time()), flush=True)
+
+
+def train_step_time(steps=10):
+    """One training step of the operator (batch 4, 64^3, width 32, 12 modes): 3 warm-up steps, then
+    the mean over `steps`."""
+    import torch
+
     from .neural import NeuralOperator
+    D, W, MX, B = 64, 32, 12, 4
     net = NeuralOperator(D=D, width=W, modes=MX, layers=4, in_ch=4, out_ch=4, max_batch=B, seed=1)
     rng = np.random.default_rng(0)
     x = torch.from_numpy(rng.normal(size=(B, 4, D, D, D)).astype(np.float32)).cuda()
@@ -114,13 +125,13 @@ def main():
         net.train_step(x, y, 1e-4)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(10):
+    for _ in range(steps):
         net.train_step(x, y, 1e-4)
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"case": "operator train step (forward, backward, Adam), batch 4, 64^3, width 32, 12 modes",
-                      "ms": e0.elapsed_time(e1) / 10}), flush=True)
     net.close()
+    return {"case": "operator train step (forward, backward, Adam), batch 4, 64^3, width 32, 12 modes",
+            "ms": e0.elapsed_time(e1) / steps}
 
 
 if __name__ == "__main__":
