@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -107,34 +108,50 @@ __global__ void k_act_bwd(const float* __restrict__ dh, const float* __restrict_
     }
 }
 
-// Per sample and channel (one block each, S values): the mean m of v = act(src) (FP64 sum, fixed
-// order) and out = bf16(v - m).  The spectral transforms take the centred field: a channel's mean
-// lives in mode (0, 0, 0) only, and the BF16 partial sums over x and y would otherwise carry it
-// into the z transform, where the modes (0, 0, kz != 0) are small differences of large rounded
-// numbers.  The mean's mode is added back in FP32 (k_add_dc).
-__global__ void __launch_bounds__(1024) k_center(const float* __restrict__ src, long long S, int use_gelu,
-                                                 bf16* __restrict__ out, float* __restrict__ mean) {
-    __shared__ double sh[32];
-    __shared__ float m_sh;
-    const long long base = (long long)blockIdx.x * S;
-    double acc = 0.0;
-    for (long long i = threadIdx.x; i < S; i += blockDim.x) {
-        const float v = src[base + i];
+// Centring of the spectral transforms' input, per sample and channel (S values each): the mean
+// m of v = act(src) and out = bf16(v - m).  The transforms take the centred field: a channel's
+// mean lives in mode (0, 0, 0) only, and the BF16 partial sums over x and y would otherwise carry
+// it into the z transform, where the modes (0, 0, kz != 0) are small differences of large rounded
+// numbers.  The mean's mode is added back in FP32 (k_add_dc).  Three passes: partial sums over
+// CENTER_PARTS chunks per channel (FP32 per thread, FP64 per block), the means in a fixed order,
+// then the element-wise centring.
+constexpr int CENTER_PARTS = 16;
+
+__global__ void __launch_bounds__(256) k_center_partials(const float* __restrict__ src, long long S, int use_gelu,
+                                                         double* __restrict__ part) {
+    const int bc = blockIdx.x / CENTER_PARTS, p = blockIdx.x % CENTER_PARTS;
+    const long long per = (S + CENTER_PARTS - 1) / CENTER_PARTS;
+    const long long lo = p * per, hi = lo + per < S ? lo + per : S;
+    const float* x = src + (long long)bc * S;
+    float acc = 0.0f;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const float v = x[i];
         acc += use_gelu ? gelu(v) : v;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-        m_sh = (float)(t / (double)S);
-        mean[blockIdx.x] = m_sh;
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
     }
-    __syncthreads();
-    const float m = m_sh;
-    for (long long i = threadIdx.x; i < S; i += blockDim.x) {
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_center_means(const double* __restrict__ part, int channels, long long S, float* __restrict__ mean) {
+    const int bc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (bc >= channels) return;
+    double t = 0.0;
+    for (int p = 0; p < CENTER_PARTS; ++p) t += part[bc * CENTER_PARTS + p];
+    mean[bc] = (float)(t / (double)S);
+}
+
+// grid (chunks, channels): each block strides over its channel's S values
+__global__ void k_center_apply(const float* __restrict__ src, long long S, int use_gelu, const float* __restrict__ mean,
+                               bf16* __restrict__ out) {
+    const long long base = (long long)blockIdx.y * S;
+    const float m = mean[blockIdx.y];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (long long)gridDim.x * blockDim.x) {
         const float v = src[base + i];
         out[base + i] = __float2bfloat16((use_gelu ? gelu(v) : v) - m);
     }
@@ -250,19 +267,27 @@ __global__ void k_mix_bwd_w(const float* __restrict__ dY, const float* __restric
     }
 }
 
-// out[i][j] += sum_{b,s} X[b][i][s] * (Y ? Y[b][j][s] : 1); one block per (i, j, chunk of the (b, s) range)
+// One chunk of the B * S positions per block, one (i, j) pair per group of blocks:
+// part[chunk][i * Cy + j] = sum over the chunk of X[b][i][s] * Y[b][j][s] (X alone if Y is null).
+// FP32 per thread (a few hundred terms at most), FP64 across the block; the chunks are summed in a
+// fixed order afterwards (k_sum_partials), so gradients are reproducible run to run.
 __global__ void k_reduce_bs(const float* __restrict__ X, const float* __restrict__ Y, int B, int Cx, int Cy, long long S,
-                            int chunks, float* __restrict__ out) {
+                            int chunks, float* __restrict__ part) {
+    const int pairs = Cx * Cy;
     const int pair = blockIdx.x / chunks, chunk = blockIdx.x % chunks;
     const int i = pair / Cy, j = pair % Cy;
     const long long n = (long long)B * S;
     const long long per = (n + chunks - 1) / chunks;
     const long long lo = chunk * per, hi = (lo + per < n) ? lo + per : n;
-    double acc = 0.0;
-    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
-        const long long b = t / S, s = t % S;
-        const float x = X[(b * Cx + i) * S + s];
-        acc += Y ? (double)x * Y[(b * Cy + j) * S + s] : (double)x;
+    float acc = 0.0f;
+    for (long long b = lo / S; b < B && b * S < hi; ++b) {
+        const long long s0 = lo > b * S ? lo - b * S : 0, s1 = hi - b * S < S ? hi - b * S : S;
+        const float* xp = X + (b * Cx + i) * S;
+        const float* yp = Y ? Y + (b * Cy + j) * S : nullptr;
+        if (yp)
+            for (long long s = s0 + threadIdx.x; s < s1; s += blockDim.x) acc = fmaf(xp[s], yp[s], acc);
+        else
+            for (long long s = s0 + threadIdx.x; s < s1; s += blockDim.x) acc += xp[s];
     }
     __shared__ double sh[256];
     sh[threadIdx.x] = acc;
@@ -271,7 +296,7 @@ __global__ void k_reduce_bs(const float* __restrict__ X, const float* __restrict
         if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) atomicAdd(&out[i * Cy + j], (float)sh[0]);
+    if (threadIdx.x == 0) part[(long long)chunk * pairs + pair] = (float)sh[0];
 }
 
 // sum of partial blocks: out[k] += sum_p part[p][k]
@@ -361,6 +386,8 @@ struct lbm_no {
     float* dyh = nullptr;
     bf16* hs = nullptr;       // centred BF16 input of the spectral transforms [B][W][S]
     float* hmean = nullptr;   // its per-(sample, channel) means [B][W]
+    double* cpart = nullptr;  // partial sums of the centring [B][W][CENTER_PARTS]
+    float* red = nullptr;     // per-chunk partials of the gradient reductions [REDUCE_CHUNKS][pairs]
     float *dh = nullptr, *dh2 = nullptr, *dz = nullptr;
     bf16* dzb = nullptr;
     float* part = nullptr;  // split-K partials of the 1x1 weight gradient
@@ -422,6 +449,25 @@ cudaError_t permute(lbm_no* n, const bf16* in, bf16* out, const long long din[6]
         total *= din[a];
     }
     k_permute6<<<grid_for(total), 256, 0, n->stream>>>(in, out, P, total);
+    return cudaGetLastError();
+}
+
+constexpr int REDUCE_CHUNKS = 64;  // chunks of the B * S positions in a gradient reduction
+
+// hs = bf16(act(src) - mean), hmean = the per-(sample, channel) means (see k_center_partials)
+cudaError_t center(lbm_no* n, const float* src, int use_gelu) {
+    const int ch = n->B * n->W;
+    k_center_partials<<<ch * CENTER_PARTS, 256, 0, n->stream>>>(src, n->S, use_gelu, n->cpart);
+    k_center_means<<<(ch + 127) / 128, 128, 0, n->stream>>>(n->cpart, ch, n->S, n->hmean);
+    k_center_apply<<<dim3(32, ch), 256, 0, n->stream>>>(src, n->S, use_gelu, n->hmean, n->hs);
+    return cudaGetLastError();
+}
+
+// out[i][j] += sum_{b,s} X[b][i][s] * (Y ? Y[b][j][s] : 1), chunk partials summed in a fixed order
+cudaError_t reduce_bs(lbm_no* n, const float* X, const float* Y, int Cx, int Cy, float* out) {
+    const int pairs = Cx * Cy;
+    k_reduce_bs<<<pairs * REDUCE_CHUNKS, 256, 0, n->stream>>>(X, Y, n->B, Cx, Cy, n->S, REDUCE_CHUNKS, n->red);
+    k_sum_partials<<<(pairs + 255) / 256, 256, 0, n->stream>>>(n->red, REDUCE_CHUNKS, pairs, out);
     return cudaGetLastError();
 }
 
@@ -498,8 +544,7 @@ lbm_status spectral_fwd(lbm_no* n, int l, const float* src, int use_gelu, float*
     const int B = n->B, W = n->W, D = n->D, MX = n->MX, MY = n->MY, MZ = n->MZ;
     const long long D2 = (long long)D * D;
     const long long BWD = (long long)B * W * D;
-    k_center<<<B * W, 1024, 0, n->stream>>>(src, n->S, use_gelu, n->hs, n->hmean);
-    NCK(n, cudaGetLastError(), "centre");
+    NCK(n, center(n, src, use_gelu), "centre");
     // x: [bcz][y][x] x FX -> t1 [bcz][(kx,ri)][y]
     NCK(n, gemm(n, D, 2 * MX, D, (int)BWD, n->hs, D, 1, D2, n->FX, 2 * MX, 1, 0, n->t1, 1, D, 2LL * MX * D, 1, 0), "fx");
     // y: rows (bcz,kx), K = (ri,y) -> t2 [b][c][z][kx][ri][ky]
@@ -540,9 +585,8 @@ lbm_status spectral_bwd(lbm_no* n, int l, const float* dz, float* dh) {
     const long long D2 = (long long)D * D;
     const long long BWD = (long long)B * W * D;
     const long long R = (long long)B * W * MX * MY;
-    // the adjoint transforms take the centred gradient too (see k_center)
-    k_center<<<B * W, 1024, 0, n->stream>>>(dz, n->S, 0, n->hs, n->hmean);
-    NCK(n, cudaGetLastError(), "centre");
+    // the adjoint transforms take the centred gradient too (see k_center_partials)
+    NCK(n, center(n, dz, 0), "centre");
     // adjoint of inverse x -> u2 layout
     NCK(n, gemm(n, D, 2 * MX, D, (int)BWD, n->hs, D, 1, D2, n->HX, 1, D, 0, n->u2, 1, D, 2LL * MX * D, 1, 0), "ix^T");
     // adjoint of inverse y -> u1p layout
@@ -618,15 +662,14 @@ lbm_status backward(lbm_no* n, const float* dout) {
     const int B = n->B, W = n->W, L = n->L;
     const long long S = n->S, tot = (long long)B * W * S;
     NCK(n, cudaMemsetAsync(n->grads, 0, sizeof(float) * n->nparam, n->stream), "zero grads");
-    const int chunks = 64;
     // projection
-    k_reduce_bs<<<n->Co * W * chunks, 256, 0, n->stream>>>(dout, n->z[L - 1], B, n->Co, W, S, chunks, n->grads + n->oQ);
-    k_reduce_bs<<<n->Co * chunks, 256, 0, n->stream>>>(dout, nullptr, B, n->Co, 1, S, chunks, n->grads + n->oq);
+    NCK(n, reduce_bs(n, dout, n->z[L - 1], n->Co, W, n->grads + n->oQ), "projection dW");
+    NCK(n, reduce_bs(n, dout, nullptr, n->Co, 1, n->grads + n->oq), "projection db");
     k_project_bwd_x<<<grid_for(tot), 256, 0, n->stream>>>(dout, n->params + n->oQ, B, W, n->Co, S, n->dh);
     NCK(n, cudaGetLastError(), "project bwd");
     for (int l = L - 1; l >= 0; --l) {
         k_act_bwd<<<grid_for(tot), 256, 0, n->stream>>>(n->dh, n->z[l], tot, l < L - 1 ? 1 : 0, n->dz, n->dzb);
-        k_reduce_bs<<<W * chunks, 256, 0, n->stream>>>(n->dz, nullptr, B, W, 1, S, chunks, n->grads + n->obc[l]);
+        NCK(n, reduce_bs(n, n->dz, nullptr, W, 1, n->grads + n->obc[l]), "bias db");
         NCK(n, cudaGetLastError(), "act bwd");
         // 1x1 weight gradient: dWc[o][c] = sum_{b,s} dz[b][o][s] h[b][c][s], split-K over s: chunks
         // of KSPLIT as one batched GEMM per sample, the remainder as one more
@@ -656,8 +699,8 @@ lbm_status backward(lbm_no* n, const float* dout) {
         std::swap(n->dh, n->dh2);
     }
     // lift
-    k_reduce_bs<<<W * n->Ci * chunks, 256, 0, n->stream>>>(n->dh, n->a_in, B, W, n->Ci, S, chunks, n->grads + n->oP);
-    k_reduce_bs<<<W * chunks, 256, 0, n->stream>>>(n->dh, nullptr, B, W, 1, S, chunks, n->grads + n->op);
+    NCK(n, reduce_bs(n, n->dh, n->a_in, W, n->Ci, n->grads + n->oP), "lift dW");
+    NCK(n, reduce_bs(n, n->dh, nullptr, W, 1, n->grads + n->op), "lift db");
     NCK(n, cudaGetLastError(), "lift bwd");
     return LBM_OK;
 }
@@ -767,6 +810,8 @@ lbm_status lbm_no_create(int D, int W, int modes, int L, int Ci, int Co, int max
     alloc((void**)&n->dzb, sizeof(bf16) * act);
     alloc((void**)&n->hs, sizeof(bf16) * act);
     alloc((void**)&n->hmean, sizeof(float) * maxB * W);
+    alloc((void**)&n->cpart, sizeof(double) * maxB * W * CENTER_PARTS);
+    alloc((void**)&n->red, sizeof(float) * REDUCE_CHUNKS * std::max(std::max(W * Ci, Co * W), W));
     alloc((void**)&n->part, sizeof(float) * maxB * ((S + KSPLIT - 1) / KSPLIT + 1) * W * W);
     alloc((void**)&n->dout, sizeof(float) * maxB * Co * S);
     alloc((void**)&n->loss_d, sizeof(double));
@@ -844,7 +889,7 @@ void lbm_no_destroy(lbm_no* n) {
     if (!n) return;
     cudaStreamSynchronize(n->stream);
     void* bufs[] = {n->params, n->grads, n->adam_m, n->adam_v, n->wcb, n->a_in, n->h0, n->FX, n->GY, n->GZ, n->HZ, n->HY,
-                    n->HX, n->t1, n->t2, n->t2p, n->yh, n->dyh, n->u1, n->u1p, n->u2, n->dh, n->dh2, n->dz, n->dzb, n->hs, n->hmean,
+                    n->HX, n->t1, n->t2, n->t2p, n->yh, n->dyh, n->u1, n->u1p, n->u2, n->dh, n->dh2, n->dz, n->dzb, n->hs, n->hmean, n->cpart, n->red,
                     n->part, n->dout, n->loss_d, n->gemm_err};
     for (void* b : bufs) cudaFree(b);
     for (bf16* b : n->hb) cudaFree(b);
