@@ -114,3 +114,47 @@ def test_batch_launch_shapes_bit_identical(shape):
         s.set_force("uniform", d["force"])
         s.step(9)
         assert np.array_equal(b.get_populations(k), s.get_populations()), (shape, k)
+
+
+@pytest.mark.parametrize("shape", [(64, 8, "strided_prefetch"), None], ids=["bench-shape", "autotuned"])
+def test_full_batch_512_channels_match_oracle(orc, shape):
+    """The batched step at the full size of the porous-channel benchmark: all 512 channels
+    (inputs.porous_channel seeds 0..511, 85.8 M nodes) in one batch with the bench's launch shape
+    (or the autotuner's), 16 of them (spread over the tile list, the largest included) started from
+    f^eq of seeded (rho, u) fields and compared, every fluid node and population, with the
+    oracle's whole-domain steps after 1 and 2 steps (both AA parities), at the per-step bound
+    64 eps32 S of the single-domain parity tests."""
+    chans = [inputs.porous_channel(sd) for sd in range(512)]
+    doms = [dict(nx=c["nx"], ny=c["ny"], nz=c["nz"], nu=c["nu"], force=(c["fx"], 0.0, 0.0), walls_y=True,
+                 mask=c["mask"]) for c in chans]
+    sizes = np.array([c["nx"] * c["ny"] * c["nz"] for c in chans])
+    pick = sorted(set(np.linspace(0, 511, 15).astype(int).tolist() + [int(np.argmax(sizes))]))
+    b = BatchSolver(doms)
+    if shape is None:
+        b.autotune(trial_steps=4)
+    else:
+        b.set_shape(*shape)
+    rng = np.random.default_rng(77)
+    start = {}
+    for k in pick:
+        d = doms[k]
+        shp = (d["nz"], d["ny"], d["nx"])
+        rho = (1.0 + 0.02 * (rng.random(shp) - 0.5)).astype(np.float32)
+        u = (0.04 * (rng.random((3,) + shp) - 0.5)).astype(np.float32)
+        b.set_state(k, rho, u[0], u[1], u[2])
+        start[k] = (rho, u)
+    for n in (1, 2):
+        b.step(1)
+        for k in pick:
+            d = doms[k]
+            og = orc.Grid(d["nx"], d["ny"], d["nz"], nu=d["nu"], walls_y=True, mask=d["mask"],
+                          collision=orc.COLL_PAPER, force_kind=orc.FORCE_UNIFORM, force=d["force"])
+            rho, u = start[k]
+            f0 = og.init_equilibrium(rho.astype(np.float64), u.astype(np.float64))
+            ref = og.step(f0, n) - orc.weights()[:, None, None, None]
+            fluid = d["mask"] == 0
+            g0 = f0 - orc.weights()[:, None, None, None]
+            S = max(np.abs(g0).max(), 0.02, abs(d["force"][0]))
+            err = np.abs(b.get_populations(k) - ref)[:, fluid].max()
+            assert err <= n * 64 * EPS32 * S, (k, n, err)
+    b.close()
