@@ -197,74 +197,105 @@ __device__ __forceinline__ long long xidx(const MixDims& d, int b, int c, int kx
 __device__ __forceinline__ long long widx(const MixDims& d, int kx, int ky, int kz, int o, int c) {
     return (((((long long)kx * d.MY + ky) * d.MZ + kz) * d.W + o) * d.W + c) * 2;
 }
-__global__ void k_mix_fwd(const float* __restrict__ X, const float* __restrict__ Wm, MixDims d, bf16* __restrict__ Y) {
-    const long long modes = (long long)d.MX * d.MY * d.MZ;
-    const long long total = (long long)d.B * d.W * modes;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int kz = (int)(idx % d.MZ);
-        const int ky = (int)((idx / d.MZ) % d.MY);
-        const int kx = (int)((idx / ((long long)d.MZ * d.MY)) % d.MX);
-        const int o = (int)((idx / modes) % d.W);
-        const int b = (int)(idx / (modes * d.W));
-        float yr = 0.0f, yi = 0.0f;
-        for (int c = 0; c < d.W; ++c) {
-            const float xr = X[xidx(d, b, c, kx, ky, 0, kz)], xi = X[xidx(d, b, c, kx, ky, 1, kz)];
-            const long long w = widx(d, kx, ky, kz, o, c);
-            const float wr = Wm[w], wi = Wm[w + 1];
-            yr += wr * xr - wi * xi;
-            yi += wr * xi + wi * xr;
+
+// Per-mode complex mixing.  One warp per Fourier mode (8 modes per block of 256 threads): the
+// warp reads the mode's W x W complex matrix once, its lanes cover the output (or input) channels,
+// and up to MIX_B samples accumulate in registers; the samples' mode coefficients are the same for
+// every lane (broadcast loads).  Each output is summed in the same order as a plain loop.
+constexpr int MIX_B = 8;
+
+__device__ __forceinline__ void mode_of(const MixDims& d, long long m, int& kx, int& ky, int& kz) {
+    kz = (int)(m % d.MZ);
+    ky = (int)((m / d.MZ) % d.MY);
+    kx = (int)(m / ((long long)d.MZ * d.MY));
+}
+
+// Y[b][o] = sum_c W[o][c] X[b][c] (complex), Y in BF16 for the inverse transforms
+__global__ void __launch_bounds__(256) k_mix_fwd(const float* __restrict__ X, const float* __restrict__ Wm, MixDims d,
+                                                 bf16* __restrict__ Y) {
+    const long long m = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (m >= (long long)d.MX * d.MY * d.MZ) return;
+    int kx, ky, kz;
+    mode_of(d, m, kx, ky, kz);
+    for (int o = threadIdx.x & 31; o < d.W; o += 32) {
+        const float* w = Wm + widx(d, kx, ky, kz, o, 0);
+        for (int b0 = 0; b0 < d.B; b0 += MIX_B) {
+            float yr[MIX_B], yi[MIX_B];
+#pragma unroll
+            for (int j = 0; j < MIX_B; ++j) yr[j] = yi[j] = 0.0f;
+            for (int c = 0; c < d.W; ++c) {
+                const float wr = w[2 * c], wi = w[2 * c + 1];
+#pragma unroll
+                for (int j = 0; j < MIX_B; ++j)
+                    if (b0 + j < d.B) {
+                        const float xr = X[xidx(d, b0 + j, c, kx, ky, 0, kz)], xi = X[xidx(d, b0 + j, c, kx, ky, 1, kz)];
+                        yr[j] += wr * xr - wi * xi;
+                        yi[j] += wr * xi + wi * xr;
+                    }
+            }
+#pragma unroll
+            for (int j = 0; j < MIX_B; ++j)
+                if (b0 + j < d.B) {
+                    Y[xidx(d, b0 + j, o, kx, ky, 0, kz)] = __float2bfloat16(yr[j]);
+                    Y[xidx(d, b0 + j, o, kx, ky, 1, kz)] = __float2bfloat16(yi[j]);
+                }
         }
-        Y[xidx(d, b, o, kx, ky, 0, kz)] = __float2bfloat16(yr);
-        Y[xidx(d, b, o, kx, ky, 1, kz)] = __float2bfloat16(yi);
     }
 }
-// dX (BF16) from dY (FP32)
-__global__ void k_mix_bwd_x(const float* __restrict__ dY, const float* __restrict__ Wm, MixDims d, bf16* __restrict__ dX) {
-    const long long modes = (long long)d.MX * d.MY * d.MZ;
-    const long long total = (long long)d.B * d.W * modes;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int kz = (int)(idx % d.MZ);
-        const int ky = (int)((idx / d.MZ) % d.MY);
-        const int kx = (int)((idx / ((long long)d.MZ * d.MY)) % d.MX);
-        const int c = (int)((idx / modes) % d.W);
-        const int b = (int)(idx / (modes * d.W));
-        float xr = 0.0f, xi = 0.0f;
+
+// dX[b][c] = sum_o conj(W[o][c]) dY[b][o] (BF16 out); lanes over c read W[o][c] coalesced
+__global__ void __launch_bounds__(256) k_mix_bwd_x(const float* __restrict__ dY, const float* __restrict__ Wm,
+                                                   MixDims d, bf16* __restrict__ dX) {
+    const long long m = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (m >= (long long)d.MX * d.MY * d.MZ) return;
+    int kx, ky, kz;
+    mode_of(d, m, kx, ky, kz);
+    for (int c = threadIdx.x & 31; c < d.W; c += 32) {
+        for (int b0 = 0; b0 < d.B; b0 += MIX_B) {
+            float xr[MIX_B], xi[MIX_B];
+#pragma unroll
+            for (int j = 0; j < MIX_B; ++j) xr[j] = xi[j] = 0.0f;
+            for (int o = 0; o < d.W; ++o) {
+                const float* w = Wm + widx(d, kx, ky, kz, o, c);
+                const float wr = w[0], wi = w[1];
+#pragma unroll
+                for (int j = 0; j < MIX_B; ++j)
+                    if (b0 + j < d.B) {
+                        const float yr = dY[xidx(d, b0 + j, o, kx, ky, 0, kz)], yi = dY[xidx(d, b0 + j, o, kx, ky, 1, kz)];
+                        xr[j] += wr * yr + wi * yi;
+                        xi[j] += -wi * yr + wr * yi;
+                    }
+            }
+#pragma unroll
+            for (int j = 0; j < MIX_B; ++j)
+                if (b0 + j < d.B) {
+                    dX[xidx(d, b0 + j, c, kx, ky, 0, kz)] = __float2bfloat16(xr[j]);
+                    dX[xidx(d, b0 + j, c, kx, ky, 1, kz)] = __float2bfloat16(xi[j]);
+                }
+        }
+    }
+}
+
+// dW[o][c] += sum_b dY[b][o] conj(X[b][c]); lanes over c write dW coalesced
+__global__ void __launch_bounds__(256) k_mix_bwd_w(const float* __restrict__ dY, const float* __restrict__ X, MixDims d,
+                                                   float* __restrict__ dW) {
+    const long long m = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (m >= (long long)d.MX * d.MY * d.MZ) return;
+    int kx, ky, kz;
+    mode_of(d, m, kx, ky, kz);
+    for (int c = threadIdx.x & 31; c < d.W; c += 32)
         for (int o = 0; o < d.W; ++o) {
-            const float yr = dY[xidx(d, b, o, kx, ky, 0, kz)], yi = dY[xidx(d, b, o, kx, ky, 1, kz)];
-            const long long w = widx(d, kx, ky, kz, o, c);
-            const float wr = Wm[w], wi = Wm[w + 1];
-            xr += wr * yr + wi * yi;
-            xi += -wi * yr + wr * yi;
+            float gr = 0.0f, gi = 0.0f;
+            for (int b = 0; b < d.B; ++b) {
+                const float yr = dY[xidx(d, b, o, kx, ky, 0, kz)], yi = dY[xidx(d, b, o, kx, ky, 1, kz)];
+                const float xr = X[xidx(d, b, c, kx, ky, 0, kz)], xi = X[xidx(d, b, c, kx, ky, 1, kz)];
+                gr += yr * xr + yi * xi;
+                gi += -yr * xi + yi * xr;
+            }
+            float* w = dW + widx(d, kx, ky, kz, o, c);
+            w[0] += gr;
+            w[1] += gi;
         }
-        dX[xidx(d, b, c, kx, ky, 0, kz)] = __float2bfloat16(xr);
-        dX[xidx(d, b, c, kx, ky, 1, kz)] = __float2bfloat16(xi);
-    }
-}
-// dW += sum_b (per mode, o, c)
-__global__ void k_mix_bwd_w(const float* __restrict__ dY, const float* __restrict__ X, MixDims d, float* __restrict__ dW) {
-    const long long modes = (long long)d.MX * d.MY * d.MZ;
-    const long long total = modes * d.W * d.W;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(idx % d.W);
-        const int o = (int)((idx / d.W) % d.W);
-        const long long m = idx / ((long long)d.W * d.W);
-        const int kz = (int)(m % d.MZ);
-        const int ky = (int)((m / d.MZ) % d.MY);
-        const int kx = (int)(m / ((long long)d.MZ * d.MY));
-        float gr = 0.0f, gi = 0.0f;
-        for (int b = 0; b < d.B; ++b) {
-            const float yr = dY[xidx(d, b, o, kx, ky, 0, kz)], yi = dY[xidx(d, b, o, kx, ky, 1, kz)];
-            const float xr = X[xidx(d, b, c, kx, ky, 0, kz)], xi = X[xidx(d, b, c, kx, ky, 1, kz)];
-            gr += yr * xr + yi * xi;
-            gi += -yr * xi + yi * xr;
-        }
-        const long long w = widx(d, kx, ky, kz, o, c);
-        dW[w] += gr;
-        dW[w + 1] += gi;
-    }
 }
 
 // One chunk of the B * S positions per block, one (i, j) pair per group of blocks:
@@ -562,7 +593,8 @@ lbm_status spectral_fwd(lbm_no* n, int l, const float* src, int use_gelu, float*
                                                          (float)n->S);
     NCK(n, cudaGetLastError(), "dc mode");
     MixDims md{B, W, MX, MY, MZ};
-    k_mix_fwd<<<grid_for((long long)B * W * MX * MY * MZ), 256, 0, n->stream>>>(n->Xh[l], n->params + n->oWm[l], md, n->yh);
+    const unsigned mix_grid = (unsigned)(((long long)MX * MY * MZ + 7) / 8);
+    k_mix_fwd<<<mix_grid, 256, 0, n->stream>>>(n->Xh[l], n->params + n->oWm[l], md, n->yh);
     NCK(n, cudaGetLastError(), "mix");
     // inverse z: rows (b,o,kx,ky), K = (ri,kz) -> u1 [b][o][kx][ky][ri][z]
     NCK(n, gemm(n, (int)R, 2 * D, 2 * MZ, 1, n->yh, 2 * MZ, 1, 0, n->HZ, 2 * D, 1, 0, n->u1, 2 * D, 1, 0, 1, 0), "iz");
@@ -603,10 +635,11 @@ lbm_status spectral_bwd(lbm_no* n, int l, const float* dz, float* dh) {
     k_add_dc<<<(B * W + 127) / 128, 128, 0, n->stream>>>(n->dyh, n->hmean, B * W, (long long)MX * MY * 2 * MZ, 1.0f);
     NCK(n, cudaGetLastError(), "dc mode");
     MixDims md{B, W, MX, MY, MZ};
-    k_mix_bwd_w<<<grid_for((long long)MX * MY * MZ * W * W), 256, 0, n->stream>>>(n->dyh, n->Xh[l], md,
+    const unsigned mix_grid = (unsigned)(((long long)MX * MY * MZ + 7) / 8);
+    k_mix_bwd_w<<<mix_grid, 256, 0, n->stream>>>(n->dyh, n->Xh[l], md,
                                                                                    n->grads + n->oWm[l]);
     NCK(n, cudaGetLastError(), "mix dW");
-    k_mix_bwd_x<<<grid_for((long long)B * W * MX * MY * MZ), 256, 0, n->stream>>>(n->dyh, n->params + n->oWm[l], md, n->yh);
+    k_mix_bwd_x<<<mix_grid, 256, 0, n->stream>>>(n->dyh, n->params + n->oWm[l], md, n->yh);
     NCK(n, cudaGetLastError(), "mix dX");
     // adjoint of forward z -> t2p layout
     NCK(n, gemm(n, (int)R, 2 * D, 2 * MZ, 1, n->yh, 2 * MZ, 1, 0, n->GZ, 1, 2 * MZ, 0, n->t2p, 2 * D, 1, 0, 1, 0), "fz^T");
