@@ -85,13 +85,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 // operand is src[r * sr + k * sk], valid for r < R, k < K; elements outside are zero.
 template <int ROWS>
 __device__ __forceinline__ void stage_tile(uint8_t* dst, const __nv_bfloat16* __restrict__ src, long long sr,
-                                           long long sk, int r0, int R, int k0, int K, int mode, int tid) {
+                                           long long sk, int r0, int R, int k0, int K, int kmax, int mode, int tid) {
+    // only the first kmax (a multiple of 16) K columns of the slice are staged: the MMAs read no more
+    const int nkc = kmax >> 3;  // 8-wide K chunks
     if (mode == STAGE_KVEC) {
         // chunk = 8 consecutive K of one row = one 16-byte core-matrix row.  Lanes: bits 0-2 the
-        // row within a core matrix (eight 16-byte rows of different banks), bits 3-4 the chunk
-        // (64 contiguous bytes of each row per warp)
-        for (int e = tid; e < ROWS * (TK / 8); e += THREADS) {
-            const int r = (e & 7) + ((e >> 6) << 3), kc = ((e >> 3) & 7) << 3;
+        // row within a core matrix (eight 16-byte rows of different banks), the next bits the chunk
+        // (contiguous bytes of each row per warp)
+        for (int e = tid; e < ROWS * nkc; e += THREADS) {
+            const int q = e >> 3;
+            // full slices (nkc = 8) by shifts; a short last slice divides
+            const int r = (e & 7) + (nkc == 8 ? (q >> 3) : q / nkc) * 8, kc = (nkc == 8 ? (q & 7) : q % nkc) << 3;
             const int row = r0 + r, kk = k0 + kc;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if (row < R && kk < K) {
@@ -111,9 +115,16 @@ __device__ __forceinline__ void stage_tile(uint8_t* dst, const __nv_bfloat16* __
         // block = 8 rows x 8 K: eight 16-byte loads (8 consecutive rows at one K each), a register
         // transpose, eight 16-byte core-matrix rows.  Lane i writes its rows starting at row
         // i mod 8, so the eight lanes of a quarter warp hit eight different bank groups.
-        for (int e = tid; e < (ROWS / 8) * (TK / 8); e += THREADS) {
+        for (int e = tid; e < (ROWS / 8) * nkc; e += THREADS) {
             const int rb = e % (ROWS / 8), kb = e / (ROWS / 8);
             const int row = r0 + rb * 8, kk = k0 + kb * 8;
+            if (kk >= K || row >= R) {
+                // a block past the end of K or of the rows: zeros, nothing to load
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    *reinterpret_cast<uint4*>(dst + core_offset(rb * 8 + i, kb * 8, ROWS)) = make_uint4(0u, 0u, 0u, 0u);
+                continue;
+            }
             uint32_t w[8][4];
             if (row + 8 <= R && kk + 8 <= K) {
 #pragma unroll
@@ -167,8 +178,8 @@ __device__ __forceinline__ void stage_tile(uint8_t* dst, const __nv_bfloat16* __
         }
     } else if (sk == 1) {
         // element by element, consecutive threads along K
-        for (int e = tid; e < ROWS * TK; e += THREADS) {
-            const int r = e / TK, k = e % TK;
+        for (int e = tid; e < ROWS * kmax; e += THREADS) {
+            const int r = e / kmax, k = e % kmax;
             const int row = r0 + r, kk = k0 + k;
             __nv_bfloat16 v = __float2bfloat16(0.0f);
             if (row < R && kk < K) v = src[(long long)row * sr + kk];
@@ -176,7 +187,7 @@ __device__ __forceinline__ void stage_tile(uint8_t* dst, const __nv_bfloat16* __
         }
     } else {
         // element by element, consecutive threads along the rows
-        for (int e = tid; e < ROWS * TK; e += THREADS) {
+        for (int e = tid; e < ROWS * kmax; e += THREADS) {
             const int r = e % ROWS, k = e / ROWS;
             const int row = r0 + r, kk = k0 + k;
             __nv_bfloat16 v = __float2bfloat16(0.0f);
@@ -231,8 +242,10 @@ __global__ void __launch_bounds__(THREADS) k_gemm_bf16_tc(GemmArgs g) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         }
         const int k0 = s * TK;
-        stage_tile<TM>(sA, A, g.sam, g.sak, m0, g.M, k0, g.K, g.a_mode, tid);
-        stage_tile<TN>(sB, B, g.sbn, g.sbk, n0, g.N, k0, g.K, g.b_mode, tid);
+        // K columns this slice multiplies: the rest of K rounded up to the MMA depth of 16
+        const int kmax = min(TK, ((g.K - k0 + 15) >> 4) << 4);
+        stage_tile<TM>(sA, A, g.sam, g.sak, m0, g.M, k0, g.K, kmax, g.a_mode, tid);
+        stage_tile<TN>(sB, B, g.sbn, g.sbk, n0, g.N, k0, g.K, kmax, g.b_mode, tid);
         // make the generic-proxy stores visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
@@ -241,6 +254,7 @@ __global__ void __launch_bounds__(THREADS) k_gemm_bf16_tc(GemmArgs g) {
             const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
 #pragma unroll
             for (int j = 0; j < TK / 16; ++j) {
+                if (16 * j >= kmax) break;  // past the end of K: no MMA on the padding
                 // K = 16 per MMA = two core matrices along K
                 const uint64_t ad = smem_desc(a_base + (uint32_t)(2 * j) * (TM >> 3) * 128, TM * 16, 128);
                 const uint64_t bd = smem_desc(b_base + (uint32_t)(2 * j) * (TN >> 3) * 128, TN * 16, 128);

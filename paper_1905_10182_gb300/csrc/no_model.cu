@@ -443,7 +443,7 @@ lbm_status ncuda(lbm_no* n, cudaError_t e, const char* what) {
         if (_e != cudaSuccess) return ncuda((n), _e, what); \
     } while (0)
 
-constexpr int KSPLIT = 8192;  // K chunk of the split-K 1x1 weight gradient
+constexpr int KSPLIT = 1024;  // K chunk of the split-K 1x1 weight gradient (256 CTAs per sample at 64^3)
 
 cudaError_t gemm(lbm_no* n, int M, int N, int K, int batch, const bf16* A, long long sam, long long sak, long long sab,
                  const bf16* Bm, long long sbk, long long sbn, long long sbb, void* C, long long scm, long long scn,
