@@ -71,3 +71,21 @@ def test_gemm_bf16_output_accumulate_alpha():
     got = C.float().cpu().numpy()
     # result rounded to BF16 once: half an ulp of 2^-8 relative, plus the accumulation bound
     _check(got, ref, 2.0 ** -8 * np.abs(ref) + 2.0 ** -20 * (np.abs(a) @ np.abs(b)))
+
+
+@pytest.mark.parametrize("M,N,K,nb", [(64, 24, 64, 1500), (40, 48, 150, 1301), (64, 64, 24, 2000)])
+def test_gemm_many_small_products(M, N, K, nb):
+    """Batches much larger than the number of CTAs, with B shared by every item (the operator's DFT
+    products): each CTA runs a run of items through the two accumulators (the last run shorter),
+    items of one or several K slices; every item against its FP64 product at the accumulation
+    bound."""
+    g = torch.Generator().manual_seed(M * 31 + nb)
+    A = torch.randn(nb, M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(K, N, generator=g).to(torch.bfloat16)
+    C = torch.empty(nb, M, N, device="cuda")
+    _gemm(M, N, K, nb, A.cuda(), (K, 1, M * K), B.cuda(), (N, 1, 0), C, (N, 1, M * N))
+    a = A.float().numpy().astype(np.float64)
+    b = B.float().numpy().astype(np.float64)
+    ref = np.einsum("imk,kn->imn", a, b)
+    bound = 2.0 ** -20 * np.einsum("imk,kn->imn", np.abs(a), np.abs(b))
+    _check(C.cpu().numpy(), ref, bound)
