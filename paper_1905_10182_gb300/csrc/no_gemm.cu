@@ -91,26 +91,38 @@ __device__ __forceinline__ void stage_tile(uint8_t* dst, const __nv_bfloat16* __
     if (mode == STAGE_KVEC) {
         // chunk = 8 consecutive K of one row = one 16-byte core-matrix row.  Lanes: bits 0-2 the
         // row within a core matrix (eight 16-byte rows of different banks), the next bits the chunk
-        // (contiguous bytes of each row per warp)
-        for (int e = tid; e < ROWS * nkc; e += THREADS) {
-            const int q = e >> 3;
-            // full slices (nkc = 8) by shifts; a short last slice divides
-            const int r = (e & 7) + (nkc == 8 ? (q >> 3) : q / nkc) * 8, kc = (nkc == 8 ? (q & 7) : q % nkc) << 3;
-            const int row = r0 + r, kk = k0 + kc;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (row < R && kk < K) {
-                const __nv_bfloat16* p = src + (long long)row * sr + kk;
-                if (kk + 8 <= K) {
-                    v = __ldg(reinterpret_cast<const uint4*>(p));
-                } else {
-                    __align__(16) __nv_bfloat16 t[8];
+        // (contiguous bytes of each row per warp).  A thread issues all its loads before its first
+        // store, so their latencies overlap.
+        constexpr int PER = (ROWS * (TK / 8) + THREADS - 1) / THREADS;  // chunks per thread, full slice
+        uint4 v[PER];
+        uint32_t dst_off[PER];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) t[j] = kk + j < K ? p[j] : __float2bfloat16(0.0f);
-                    v = *reinterpret_cast<const uint4*>(t);
+        for (int t = 0; t < PER; ++t) {
+            const int e = tid + t * THREADS;
+            v[t] = make_uint4(0u, 0u, 0u, 0u);
+            dst_off[t] = 0xFFFFFFFFu;
+            if (e < ROWS * nkc) {
+                const int q = e >> 3;
+                // full slices (nkc = 8) by shifts; a short last slice divides
+                const int r = (e & 7) + (nkc == 8 ? (q >> 3) : q / nkc) * 8, kc = (nkc == 8 ? (q & 7) : q % nkc) << 3;
+                const int row = r0 + r, kk = k0 + kc;
+                dst_off[t] = core_offset(r, kc, ROWS);
+                if (row < R && kk < K) {
+                    const __nv_bfloat16* p = src + (long long)row * sr + kk;
+                    if (kk + 8 <= K) {
+                        v[t] = __ldg(reinterpret_cast<const uint4*>(p));
+                    } else {
+                        __align__(16) __nv_bfloat16 tmp[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) tmp[j] = kk + j < K ? p[j] : __float2bfloat16(0.0f);
+                        v[t] = *reinterpret_cast<const uint4*>(tmp);
+                    }
                 }
             }
-            *reinterpret_cast<uint4*>(dst + core_offset(r, kc, ROWS)) = v;
         }
+#pragma unroll
+        for (int t = 0; t < PER; ++t)
+            if (dst_off[t] != 0xFFFFFFFFu) *reinterpret_cast<uint4*>(dst + dst_off[t]) = v[t];
     } else if (mode == STAGE_ROWVEC) {
         // block = 8 rows x 8 K: eight 16-byte loads (8 consecutive rows at one K each), a register
         // transpose, eight 16-byte core-matrix rows.  Lane i writes its rows starting at row
