@@ -1,18 +1,24 @@
 // BF16 tensor-core GEMM for the neural-operator warm start (5th-generation tensor cores, sm_103a):
 //   C[b] (+)= A[b] x B[b],  A: M x K, B: K x N (BF16), accumulation in FP32 in tensor memory.
 // Each operand is addressed through one stride per dimension plus a batch stride, so transposed
-// and permuted views need no copies.  A CTA computes a 128 x TN tile of C (TN = 32, 48 or 64, the
-// smallest that covers N, so the operator's 24- and 48-column DFT products fill their tiles).  Its
-// 128 threads stage 64-deep K slices of A and B into shared memory in the canonical no-swizzle
-// K-major layout of 8 x 16-byte core matrices, in two stages: while the tensor core runs the
-// MMAs of one slice, the threads stage the next into the other stage.  One elected thread issues
-// four tcgen05.mma (K = 16 each) per slice and commits them to that stage's mbarrier; after the
-// last slice each warp reads its 32 accumulator lanes back with tcgen05.ld.
-// Staging moves 16 bytes per access when an operand allows it: a K-contiguous operand copies
-// whole core-matrix rows (8 consecutive K elements); a row-contiguous one (M or N fastest) loads
-// 8 x 8 element blocks (8 rows at each of 8 K) and transposes them in registers with byte
-// permutes.  Other layouts (or unaligned ones) go element by element.  Every mbarrier wait is
-// bounded: on timeout the kernel records an error, still frees its tensor memory and returns.
+// and permuted views need no copies.  Two kernels:
+// * k_gemm_bf16_tma, for operands the tensor memory accelerator can address (16-byte aligned
+//   base, strides multiples of 8 elements, K- or M/N-contiguous): persistent blocks, one per SM,
+//   warp-specialised.  One thread streams 64-deep K blocks of A (128 rows) and B (64, 128 or 256
+//   columns) into a ring of shared-memory stages with cp.async.bulk.tensor (128-byte swizzle,
+//   rows outside the operand zero-filled), one thread issues tcgen05.mma into two tensor-memory
+//   accumulators, and two groups of four warps drain the accumulators (tcgen05.ld) and store C
+//   while the next tile is loaded and multiplied.  Items of at most 64 rows against a shared B
+//   are stacked two to a 128-row tile.
+// * k_gemm_bf16_tc, for every other operand: a CTA computes one 128 x TN tile of C (TN = 32, 48
+//   or 64); its 128 threads stage 64-deep K slices of A and B into shared memory in the
+//   no-swizzle K-major layout of 8 x 16-byte core matrices, in two stages, one elected thread
+//   issues the MMAs.  Staging moves 16 bytes per access where the operand allows it (whole
+//   core-matrix rows of a K-contiguous operand; 8 x 8 blocks of a row-contiguous one, transposed
+//   in registers with byte permutes), else element by element.
+// Every mbarrier wait is bounded: on timeout the kernel records an error, waits (bounded) for its
+// copies and MMAs in flight, frees its tensor memory and returns.
+#include <cuda.h>  // CUtensorMap and the tensor-map encoder (resolved through the runtime at first use)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -351,6 +357,332 @@ __global__ void __launch_bounds__(THREADS) k_gemm_bf16_tc(GemmArgs g) {
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// TMA path: a persistent, warp-specialised kernel for operands that the tensor memory accelerator
+// can address (16-byte aligned base, 16-byte multiple strides, one unit-stride dimension).
+//   warp 0 (one lane)  TMA producer: 64-deep K blocks of A (128 rows) and B (TN rows) into a ring
+//                      of STAGES shared-memory stages, each signalled by its `full` mbarrier with
+//                      the byte count of the copies;
+//   warp 1 (one lane)  MMA issuer: waits for a stage, issues up to four tcgen05.mma (K = 16) into
+//                      one of two TMEM accumulators, commits the stage back to its `empty` barrier
+//                      and, after a tile's last block, the accumulator to its `tfull` barrier;
+//   warps 2-5          epilogue: read the finished accumulator (each warp its 32-lane quarter),
+//                      hand it back through `tempty`, scale and store C.
+// The producer runs ahead across tile boundaries, so the loads of the next tile overlap the MMAs
+// and the epilogue of the current one.  Tiles are 128-byte swizzled: a K-major operand is loaded
+// as rows of 64 K elements (128 B), an M- or N-major one as K rows of 64 M or N elements; rows
+// outside the operand are zero-filled by the copy.
+namespace tma {
+
+constexpr int THREADS = 320;            // warps 0-1 roles, 2-5 and 6-9 the two epilogue groups
+constexpr int ATOM = 64;                 // elements in one swizzled 128-byte row
+constexpr int A_STAGE = TM * TK * 2;     // 16 KB: 128 rows x 64 K
+constexpr int SMEM_ALIGN = 1024;         // the 128-byte swizzle repeats every 8 rows = 1024 B
+// Unused shared memory after the ring: a descriptor whose two strides were read the other way
+// round would still address memory of this block.
+constexpr int SMEM_TAIL = 8192;
+
+struct Args {
+    int M, N, K, batch;
+    int tiles_m, tiles_n, k_blocks;
+    int pack;  // 2: two batch items (M <= 64, B shared) stacked in one 128-row tile; else 1
+    long long tiles;
+    int a_mn, b_mn;  // operand M- (N-) contiguous rather than K-contiguous
+    int a_3d, b_3d;  // tensor map carries the batch as its third dimension
+    void* C;
+    long long scm, scn, scb;
+    int out_bf16;
+    float alpha;
+    int beta;
+    int c_vec;
+    unsigned int* err;
+};
+
+// tcgen05 shared-memory descriptor with 128-byte swizzling (layout type 2 at bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return smem_desc(saddr, lbo, sbo) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort) {
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < WAIT_POLLS; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 1023) == 1023 && (*abort || global_ns() - t0 > WAIT_NS)) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, bool three,
+                                         uint32_t bar) {
+    const uint64_t m = reinterpret_cast<uint64_t>(map);
+    if (three)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];\n" ::"r"(dst),
+            "l"(m), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+            : "memory");
+    else
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+            "[%4];\n" ::"r"(dst),
+            "l"(m), "r"(c0), "r"(c1), "r"(bar)
+            : "memory");
+}
+
+// Tile t of the schedule: first batch item b, first row m0, column tile tn (N fastest, then M,
+// then batch items, `pack` items per tile).
+__device__ __forceinline__ void tile_coords(const Args& g, long long t, int& b, int& m0, int& tn) {
+    const long long per = (long long)g.tiles_m * g.tiles_n;
+    const long long bt = t / per;
+    const int r = (int)(t - bt * per);
+    b = (int)bt * g.pack;
+    m0 = (r / g.tiles_n) * TM;
+    tn = r % g.tiles_n;
+}
+
+// One accumulator chunk of 16 FP32 columns (tcgen05.ld 32 lanes x 32 bit, 16 repetitions); the
+// caller issues several before one tcgen05.wait::ld.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+// C (+)= alpha * acc for 16 columns n, n + 1, ... of one row (off0: element offset of (row, n)).
+__device__ __forceinline__ void store16(const Args& g, long long off0, int n, const uint32_t (&v)[16]) {
+    if (g.c_vec && n + 16 <= g.N) {
+        float4* C4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.C) + off0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float4 o = make_float4(g.alpha * __uint_as_float(v[4 * q]), g.alpha * __uint_as_float(v[4 * q + 1]),
+                                   g.alpha * __uint_as_float(v[4 * q + 2]), g.alpha * __uint_as_float(v[4 * q + 3]));
+            if (g.beta) {
+                const float4 p = C4[q];
+                o.x += p.x;
+                o.y += p.y;
+                o.z += p.z;
+                o.w += p.w;
+            }
+            C4[q] = o;
+        }
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (n + j >= g.N) break;
+        const float val = g.alpha * __uint_as_float(v[j]);
+        const long long off = off0 + (long long)j * g.scn;
+        if (g.out_bf16) {
+            __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(g.C) + off;
+            *C = __float2bfloat16(g.beta ? __bfloat162float(*C) + val : val);
+        } else {
+            float* C = reinterpret_cast<float*>(g.C) + off;
+            *C = g.beta ? *C + val : val;
+        }
+    }
+}
+
+template <int TN, int STAGES>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_gemm_bf16_tma(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, Args g) {
+    constexpr int B_STAGE = TN * TK * 2;
+    constexpr int STAGE = A_STAGE + B_STAGE;
+    constexpr uint32_t TMEM_COLS = 2 * TN;  // two accumulators of 128 lanes x TN FP32 columns
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t ring = (smem_u32(smem_raw) + SMEM_ALIGN - 1) & ~(uint32_t)(SMEM_ALIGN - 1);
+
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[s])) : "memory");
+        }
+        for (int a = 0; a < 2; ++a) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&tfull[a])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(&tempty[a])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&drain)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        uint32_t it = 0;
+        for (long long t = blockIdx.x; t < g.tiles && !abort_flag; t += gridDim.x) {
+            int b, m0, tn;
+            tile_coords(g, t, b, m0, tn);
+            const int n0 = tn * TN;
+            for (int kb = 0; kb < g.k_blocks; ++kb, ++it) {
+                const uint32_t s = it % STAGES, use = it / STAGES;
+                if (!wait_or_abort(smem_u32(&empty[s]), (use & 1) ^ 1, &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                const uint32_t bar = smem_u32(&full[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(STAGE)
+                             : "memory");
+                const uint32_t sa = ring + s * STAGE, sb = sa + A_STAGE;
+                const int k0 = kb * TK;
+                if (g.a_mn) {
+                    // two 64-row atoms: rows m0 .. m0 + 127 of one item, or (packed) rows 0 .. 63 of
+                    // items b and b + 1 in one box
+                    tma_load(sa, &map_a, m0, k0, b, g.a_3d, bar);
+                    if (g.pack == 1) tma_load(sa + ATOM * TK * 2, &map_a, m0 + ATOM, k0, b, g.a_3d, bar);
+                } else {
+                    tma_load(sa, &map_a, k0, m0, b, g.a_3d, bar);
+                }
+                if (g.b_mn) {
+#pragma unroll
+                    for (int j = 0; j < TN / ATOM; ++j) tma_load(sb + j * ATOM * TK * 2, &map_b, n0 + j * ATOM, k0, b, g.b_3d, bar);
+                } else {
+                    tma_load(sb, &map_b, k0, n0, b, g.b_3d, bar);
+                }
+            }
+        }
+        // every copy issued has landed before the block can exit: wait for the last phase of each
+        // stage that was used (at once on a normal exit)
+        for (uint32_t s = 0; s < STAGES && s < it; ++s) {
+            const uint32_t last = it - 1 - ((it - 1 + STAGES - s) % STAGES);  // last iteration on stage s
+            volatile int never = 0;
+            if (!wait_or_abort(smem_u32(&full[last % STAGES]), (last / STAGES) & 1, &never)) atomicOr(g.err, 1u);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        const uint32_t idesc = instr_desc(TM, TN) | ((uint32_t)g.a_mn << 15) | ((uint32_t)g.b_mn << 16);
+        uint32_t it = 0, lt = 0;
+        for (long long t = blockIdx.x; t < g.tiles && !abort_flag; t += gridDim.x, ++lt) {
+            const uint32_t a = lt & 1, ause = lt >> 1;
+            if (!wait_or_abort(smem_u32(&tempty[a]), (ause & 1) ^ 1, &abort_flag)) {
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t d = tmem + a * TN;
+            bool ok = true;
+            for (int kb = 0; kb < g.k_blocks; ++kb, ++it) {
+                const uint32_t s = it % STAGES, use = it / STAGES;
+                if (!wait_or_abort(smem_u32(&full[s]), use & 1, &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t sa = ring + s * STAGE, sb = sa + A_STAGE;
+                const int kmax = min(TK, ((g.K - kb * TK + 15) >> 4) << 4);
+#pragma unroll
+                for (int j = 0; j < TK / 16; ++j) {
+                    if (16 * j >= kmax) break;  // zero padding past the end of K: no MMA
+                    // K-major: the 16-deep step is 32 B further along each swizzled row; M/N-major:
+                    // 16 K rows = two 1024-byte groups further, atoms of 64 rows 8 KB apart
+                    const uint64_t ad = g.a_mn ? sw128_desc(sa + 2048u * j, ATOM * TK * 2, 1024)
+                                               : sw128_desc(sa + 32u * j, 16, 1024);
+                    const uint64_t bd = g.b_mn ? sw128_desc(sb + 2048u * j, ATOM * TK * 2, 1024)
+                                               : sw128_desc(sb + 32u * j, 16, 1024);
+                    const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 smem_u32(&empty[s]))
+                             : "memory");
+            }
+            if (!ok) {
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&tfull[a]))
+                         : "memory");
+        }
+        // no MMA of this thread may still run when the tensor memory is freed
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         smem_u32(&drain))
+                     : "memory");
+        volatile int never = 0;
+        if (!wait_or_abort(smem_u32(&drain), 0, &never)) atomicOr(g.err, 1u);
+    } else if (warp >= 2) {
+        // ---- epilogue: group e (warps 2-5 or 6-9) takes the tiles of accumulator e; warp w reads
+        // accumulator lanes 32 (w mod 4) .. + 31
+        const int q = warp & 3, grp = (warp - 2) >> 2;
+        uint32_t lt = 0;
+        for (long long t = blockIdx.x; t < g.tiles && !abort_flag; t += gridDim.x, ++lt) {
+            const uint32_t a = lt & 1, ause = lt >> 1;
+            if ((int)a != grp) continue;
+            int b, m0, tn;
+            tile_coords(g, t, b, m0, tn);
+            const int n0 = tn * TN;
+            if (!wait_or_abort(smem_u32(&tfull[a]), ause & 1, &abort_flag)) {
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const int r = q * 32 + lane;  // row of the tile
+            const int item = g.pack == 2 ? b + (r >> 6) : b, row = g.pack == 2 ? (r & 63) : m0 + r;
+            const bool live = row < g.M && item < g.batch;
+            const long long rowoff = (long long)item * g.scb + (long long)row * g.scm;
+            const int ncols = min(TN, g.N - n0);
+            for (int c0 = 0; c0 < ncols; c0 += 64) {
+                // up to four 16-column loads in flight, then one wait
+                uint32_t v[4][16];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * TN + (uint32_t)c0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (c0 + 16 * j < ncols) tmem_ld16(taddr + 16 * j, v[j]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                if (live) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (c0 + 16 * j < ncols) {
+                            const int n = n0 + c0 + 16 * j;
+                            store16(g, rowoff + (long long)n * g.scn, n, v[j]);
+                        }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&tempty[a])) : "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && abort_flag) atomicOr(g.err, 1u);
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+}  // namespace tma
+
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Staging mode of an operand whose element (r, k) is at base + r * sr + k * sk (+ b * sb).
@@ -379,12 +711,140 @@ cudaError_t launch_tn(const GemmArgs& g, int batch, cudaStream_t st) {
 
 }  // namespace
 
+namespace {
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no link against libcuda).
+EncodeTiled encoder() {
+    static const EncodeTiled fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<EncodeTiled>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of an operand whose element (r, k) of batch item b sits at base + r sr + k sk + b sb
+// (elements), r < R, k < K.  A K-contiguous operand (sk = 1) is described K-fastest with boxes of
+// 64 K x box_rows rows x box_items items; an R-contiguous one (sr = 1) R-fastest with boxes of 64
+// rows x 64 K x box_items items.  Both use the 128-byte swizzle.  Returns false when the copy engine
+// cannot address the operand: base not 16-byte aligned, a stride that is not a positive multiple
+// of 8 elements, no unit stride.
+bool operand_map(CUtensorMap* map, const void* base, int R, int K, int batch, long long sr, long long sk, long long sb,
+                 int box_rows, int box_items, int* mn_major, int* three) {
+    const EncodeTiled enc = encoder();
+    if (!enc || !aligned16(base)) return false;
+    cuuint64_t dims[3], strides[2];
+    cuuint32_t box[3], estr[3] = {1, 1, 1};
+    if (sk == 1 && sr > 0 && sr % 8 == 0) {
+        *mn_major = 0;
+        dims[0] = (cuuint64_t)K;
+        dims[1] = (cuuint64_t)R;
+        strides[0] = (cuuint64_t)sr * 2;
+        box[0] = tma::ATOM;
+        box[1] = (cuuint32_t)box_rows;
+    } else if (sr == 1 && sk > 0 && sk % 8 == 0) {
+        *mn_major = 1;
+        dims[0] = (cuuint64_t)R;
+        dims[1] = (cuuint64_t)K;
+        strides[0] = (cuuint64_t)sk * 2;
+        box[0] = tma::ATOM;
+        box[1] = TK;
+    } else {
+        return false;
+    }
+    *three = batch > 1 && sb != 0;
+    if (box_items > 1 && !*three) return false;
+    if (*three) {
+        if (sb < 0 || sb % 8 != 0) return false;
+        dims[2] = (cuuint64_t)batch;
+        strides[1] = (cuuint64_t)sb * 2;
+        box[2] = (cuuint32_t)box_items;
+    }
+    for (int i = 0; i < 1 + *three; ++i)
+        if (strides[i] >= (1ull << 40)) return false;
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, *three ? 3 : 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        n = 0;
+    return n > 0 ? n : 1;
+}
+
+template <int TN, int STAGES>
+cudaError_t launch_tma_tn(const CUtensorMap& ma, const CUtensorMap& mb, tma::Args a, int batch, cudaStream_t st) {
+    constexpr int smem = STAGES * (tma::A_STAGE + TN * TK * 2) + tma::SMEM_ALIGN + tma::SMEM_TAIL;
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(tma::k_gemm_bf16_tma<TN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    a.tiles_n = (a.N + TN - 1) / TN;
+    a.tiles = (long long)a.tiles_m * a.tiles_n * ((batch + a.pack - 1) / a.pack);
+    static const int sms = sm_count();
+    const long long grid = a.tiles < sms ? a.tiles : sms;
+    tma::k_gemm_bf16_tma<TN, STAGES><<<(unsigned)grid, tma::THREADS, smem, st>>>(ma, mb, a);
+    return cudaGetLastError();
+}
+
+// The TMA kernel when both operands allow it (and K > 0); false: use the register-staged kernel.
+bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* err) {
+    if (g.K <= 0) return false;
+    const int TN = g.N <= 64 ? 64 : (g.N <= 128 ? 128 : 256);
+    CUtensorMap ma, mb;
+    tma::Args a;
+    // items of at most 64 rows against one shared B: two per 128-row tile
+    a.pack = (g.M <= tma::ATOM && batch > 1 && g.sbb == 0 && g.sab != 0) ? 2 : 1;
+    if (!operand_map(&ma, g.A, g.M, g.K, batch, g.sam, g.sak, g.sab, TM / a.pack, a.pack, &a.a_mn, &a.a_3d))
+        return false;
+    if (!operand_map(&mb, g.B, g.N, g.K, batch, g.sbn, g.sbk, g.sbb, TN, 1, &a.b_mn, &a.b_3d)) return false;
+    a.M = g.M;
+    a.N = g.N;
+    a.K = g.K;
+    a.batch = batch;
+    a.tiles_m = (g.M + TM - 1) / TM;
+    a.k_blocks = (g.K + TK - 1) / TK;
+    a.C = g.C;
+    a.scm = g.scm;
+    a.scn = g.scn;
+    a.scb = g.scb;
+    a.out_bf16 = g.out_bf16;
+    a.alpha = g.alpha;
+    a.beta = g.beta;
+    a.c_vec = g.c_vec;
+    a.err = g.err;
+    if (TN == 64)
+        *err = launch_tma_tn<64, 8>(ma, mb, a, batch, st);
+    else if (TN == 128)
+        *err = launch_tma_tn<128, 6>(ma, mb, a, batch, st);
+    else
+        *err = launch_tma_tn<256, 4>(ma, mb, a, batch, st);
+    return true;
+}
+
+}  // namespace
+
 cudaError_t launch_gemm_bf16(const GemmArgs& g_in, int batch, cudaStream_t st) {
     if (g_in.M <= 0 || g_in.N <= 0 || g_in.K < 0 || batch <= 0) return cudaErrorInvalidValue;
     GemmArgs g = g_in;
+    g.c_vec = !g.out_bf16 && g.scn == 1 && g.scm % 4 == 0 && (batch == 1 || g.scb % 4 == 0) && aligned16(g.C);
+    cudaError_t e = cudaSuccess;
+    if (try_launch_tma(g, batch, st, &e)) return e;
     g.a_mode = stage_mode(g.A, g.sam, g.sak, g.sab, batch);
     g.b_mode = stage_mode(g.B, g.sbn, g.sbk, g.sbb, batch);
-    g.c_vec = !g.out_bf16 && g.scn == 1 && g.scm % 4 == 0 && (batch == 1 || g.scb % 4 == 0) && aligned16(g.C);
     if (g.N <= 32) return launch_tn<32>(g, batch, st);
     if (g.N <= 48) return launch_tn<48>(g, batch, st);
     return launch_tn<64>(g, batch, st);

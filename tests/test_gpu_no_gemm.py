@@ -76,9 +76,9 @@ def test_gemm_bf16_output_accumulate_alpha():
 @pytest.mark.parametrize("M,N,K,nb", [(64, 24, 64, 1500), (40, 48, 150, 1301), (64, 64, 24, 2000)])
 def test_gemm_many_small_products(M, N, K, nb):
     """Batches much larger than the number of CTAs, with B shared by every item (the operator's DFT
-    products): each CTA runs a run of items through the two accumulators (the last run shorter),
-    items of one or several K slices; every item against its FP64 product at the accumulation
-    bound."""
+    products): items of one or several K slices, through the copy-engine path (K = 64 and 24:
+    persistent blocks, two items per tile) and the register-staged one (K = 150, rows not 16-byte
+    aligned); every item against its FP64 product at the accumulation bound."""
     g = torch.Generator().manual_seed(M * 31 + nb)
     A = torch.randn(nb, M, K, generator=g).to(torch.bfloat16)
     B = torch.randn(K, N, generator=g).to(torch.bfloat16)
@@ -89,3 +89,66 @@ def test_gemm_many_small_products(M, N, K, nb):
     ref = np.einsum("imk,kn->imn", a, b)
     bound = 2.0 ** -20 * np.einsum("imk,kn->imn", np.abs(a), np.abs(b))
     _check(C.cpu().numpy(), ref, bound)
+
+
+def _operand(rng, rows, K, nb, k_major, pad):
+    """Rows x K BF16 operand of nb items, stored K-contiguous (k_major) or rows-contiguous, the
+    contiguous extent rounded up to a multiple of 8 and padded by `pad` more elements; returns (host array [nb, rows, K], device
+    storage, (s_row, s_k, s_batch)); nb = 0 stores one item shared by every batch item."""
+    items = max(nb, 1)
+    x = torch.from_numpy(rng.normal(size=(items, rows, K)).astype(np.float32)).to(torch.bfloat16)
+    if k_major:
+        ld = -(-K // 8) * 8 + pad
+        store = torch.zeros(items, rows, ld, dtype=torch.bfloat16)
+        store[:, :, :K] = x
+        strides = (ld, 1, rows * ld if nb else 0)
+    else:
+        ld = -(-rows // 8) * 8 + pad
+        store = torch.zeros(items, K, ld, dtype=torch.bfloat16)
+        store[:, :, :rows] = x.transpose(1, 2)
+        strides = (1, ld, K * ld if nb else 0)
+    return x.float().numpy().astype(np.float64), store.cuda(), strides
+
+
+@pytest.mark.parametrize("a_k,b_k", [(True, True), (True, False), (False, True), (False, False)])
+@pytest.mark.parametrize("M,N,K,nb,b_shared", [(200, 40, 72, 3, False), (130, 120, 200, 2, True),
+                                                (300, 264, 136, 1, False), (64, 24, 64, 700, True),
+                                                (40, 48, 136, 301, True)])
+def test_gemm_tma_operand_layouts(a_k, b_k, M, N, K, nb, b_shared):
+    """Operands the copy engine can address (16-byte aligned, strides multiples of 8 elements):
+    each of A and B K-contiguous or M/N-contiguous, ragged M, N and K (K a multiple of 8 but not
+    of 64), batched items or one B shared by all, tiles 64, 128 and 256 columns wide, and items
+    of at most 64 rows against a shared B (two items per 128-row tile; an odd count leaves the
+    last tile half empty)."""
+    rng = np.random.default_rng(M * 13 + N * 7 + K + 2 * a_k + b_k)
+    a, Ad, sa = _operand(rng, M, K, nb, a_k, 8)
+    b, Bd, sbt = _operand(rng, N, K, 0 if b_shared else nb, b_k, 16)   # stored as N x K
+    sb = (sbt[1], sbt[0], sbt[2])                                       # (s_k, s_n, s_batch)
+    C = torch.zeros(nb, M, N, device="cuda")
+    _gemm(M, N, K, nb, Ad, sa, Bd, sb, C, (N, 1, M * N))
+    bt = np.broadcast_to(b, (nb, N, K)) if b_shared else b
+    ref = np.einsum("imk,ink->imn", a, bt)
+    bound = 2.0 ** -20 * np.einsum("imk,ink->imn", np.abs(a), np.abs(bt))
+    _check(C.cpu().numpy(), ref, bound)
+
+
+@pytest.mark.parametrize("out_bf16", [0, 1])
+def test_gemm_tma_alpha_beta_column_major_c(out_bf16):
+    """The copy-engine path's epilogue: C column-major (M contiguous), alpha = -0.75, added to the
+    previous C (beta), FP32 or BF16 output."""
+    M, N, K, nb = 260, 72, 96, 2
+    rng = np.random.default_rng(77 + out_bf16)
+    a, Ad, sa = _operand(rng, M, K, nb, True, 0)
+    b, Bd, sbt = _operand(rng, N, K, nb, False, 8)
+    sb = (sbt[1], sbt[0], sbt[2])
+    c0 = rng.normal(size=(nb, N, M)).astype(np.float32)                 # C[b][m][n] at (b, n, m)
+    dt = torch.bfloat16 if out_bf16 else torch.float32
+    C = torch.from_numpy(c0).to(dt).cuda()
+    c0 = C.float().cpu().numpy().astype(np.float64)
+    _gemm(M, N, K, nb, Ad, sa, Bd, sb, C, (1, M, N * M), out_bf16=out_bf16, alpha=-0.75, beta=1)
+    prod = np.einsum("imk,ink->inm", a, b)
+    ref = c0 - 0.75 * prod
+    bound = 0.75 * 2.0 ** -20 * np.einsum("imk,ink->inm", np.abs(a), np.abs(b))
+    if out_bf16:
+        bound = bound + 2.0 ** -8 * np.abs(ref)
+    _check(C.float().cpu().numpy(), ref, bound)
