@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(THREADS) k_gemm_bf16_tc(GemmArgs g) {
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
             if (row < g.M) {
                 const long long off0 = bz * g.scb + (long long)row * g.scm + (long long)(n0 + c) * g.scn;
-                if (g.c_vec && n0 + c + 16 <= g.N) {
+                if (g.c_vec == 1 && n0 + c + 16 <= g.N) {
                     // 16 consecutive FP32 columns of one row, 16-byte aligned: four vector stores
                     float4* C4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.C) + off0);
 #pragma unroll
@@ -360,35 +360,46 @@ __global__ void __launch_bounds__(THREADS) k_gemm_bf16_tc(GemmArgs g) {
 // ---------------------------------------------------------------------------------------------
 // TMA path: a persistent, warp-specialised kernel for operands that the tensor memory accelerator
 // can address (16-byte aligned base, 16-byte multiple strides, one unit-stride dimension).
-//   warp 0 (one lane)  TMA producer: 64-deep K blocks of A (128 rows) and B (TN rows) into a ring
-//                      of STAGES shared-memory stages, each signalled by its `full` mbarrier with
-//                      the byte count of the copies;
+//   warp 0 (one lane)  TMA producer: K blocks of A (128 rows) and B (TN rows) into a ring of
+//                      shared-memory stages, each signalled by its `full` mbarrier with the byte
+//                      count of the copies;
 //   warp 1 (one lane)  MMA issuer: waits for a stage, issues up to four tcgen05.mma (K = 16) into
 //                      one of two TMEM accumulators, commits the stage back to its `empty` barrier
 //                      and, after a tile's last block, the accumulator to its `tfull` barrier;
-//   warps 2-5          epilogue: read the finished accumulator (each warp its 32-lane quarter),
-//                      hand it back through `tempty`, scale and store C.
-// The producer runs ahead across tile boundaries, so the loads of the next tile overlap the MMAs
-// and the epilogue of the current one.  Tiles are 128-byte swizzled: a K-major operand is loaded
-// as rows of 64 K elements (128 B), an M- or N-major one as K rows of 64 M or N elements; rows
-// outside the operand are zero-filled by the copy.
+//   warps 2-5, 6-9     epilogue, one group per accumulator: read it back (each warp its 32-lane
+//                      quarter), hand it back through `tempty`, scale and store C.
+// The producer runs ahead across tile boundaries, so the loads of the next tiles overlap the MMAs
+// and the epilogue of the current one.  A B shared by every batch item whose K blocks fit in
+// shared memory (the operator's DFT matrices and 1x1 weights) is loaded once per block and stays
+// resident; the ring then carries A alone, in as many stages as fit.  Tiles are 128-byte swizzled:
+// a K-major operand is loaded as rows of 64 K elements (128 B), an M- or N-major one as K rows of
+// 64 M or N elements (an M-major A only as deep in K as K needs); rows outside the operand are
+// zero-filled by the copy.
 namespace tma {
 
-constexpr int THREADS = 320;            // warps 0-1 roles, 2-5 and 6-9 the two epilogue groups
+constexpr int THREADS = 320;             // warps 0-1 roles, 2-5 and 6-9 the two epilogue groups
 constexpr int ATOM = 64;                 // elements in one swizzled 128-byte row
-constexpr int A_STAGE = TM * TK * 2;     // 16 KB: 128 rows x 64 K
+constexpr int MAX_STAGES = 16;
 constexpr int SMEM_ALIGN = 1024;         // the 128-byte swizzle repeats every 8 rows = 1024 B
+constexpr int SMEM_USE = 200 * 1024;     // resident B + ring
 // Unused shared memory after the ring: a descriptor whose two strides were read the other way
 // round would still address memory of this block.
 constexpr int SMEM_TAIL = 8192;
+constexpr int SMEM_BYTES = SMEM_USE + SMEM_ALIGN + SMEM_TAIL;
 
 struct Args {
     int M, N, K, batch;
     int tiles_m, tiles_n, k_blocks;
     int pack;  // 2: two batch items (M <= 64, B shared) stacked in one 128-row tile; else 1
     long long tiles;
-    int a_mn, b_mn;  // operand M- (N-) contiguous rather than K-contiguous
-    int a_3d, b_3d;  // tensor map carries the batch as its third dimension
+    int a_mn, b_mn;   // operand M- (N-) contiguous rather than K-contiguous
+    int a_3d, b_3d;   // tensor map carries the batch as its third dimension
+    int a_kbox;       // K depth of an M-major A box (64, or K rounded up to 16 when K < 64)
+    int a_bytes;      // bytes of one A block (128 rows x 64 K, or 2 atoms x a_kbox K rows)
+    int b_res;        // B loaded once (every K block of the single column tile) and kept
+    int stages;       // ring stages
+    int stage_bytes;  // A block (+ B block unless resident)
+    int res_bytes;    // resident B region ahead of the ring (0 if none)
     void* C;
     long long scm, scn, scb;
     int out_bf16;
@@ -458,52 +469,82 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 }
 
 // C (+)= alpha * acc for 16 columns n, n + 1, ... of one row (off0: element offset of (row, n)).
+// With beta every load of the old C is issued before the first store.
 __device__ __forceinline__ void store16(const Args& g, long long off0, int n, const uint32_t (&v)[16]) {
-    if (g.c_vec && n + 16 <= g.N) {
+    const bool whole = n + 16 <= g.N;
+    if (whole && g.c_vec == 1) {
+        // FP32, row-contiguous: four 16-byte vectors
         float4* C4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.C) + off0);
+        float4 old[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float4 o = make_float4(g.alpha * __uint_as_float(v[4 * q]), g.alpha * __uint_as_float(v[4 * q + 1]),
-                                   g.alpha * __uint_as_float(v[4 * q + 2]), g.alpha * __uint_as_float(v[4 * q + 3]));
-            if (g.beta) {
-                const float4 p = C4[q];
-                o.x += p.x;
-                o.y += p.y;
-                o.z += p.z;
-                o.w += p.w;
+        for (int q = 0; q < 4; ++q) old[q] = g.beta ? C4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            C4[q] = make_float4(old[q].x + g.alpha * __uint_as_float(v[4 * q]), old[q].y + g.alpha * __uint_as_float(v[4 * q + 1]),
+                                old[q].z + g.alpha * __uint_as_float(v[4 * q + 2]),
+                                old[q].w + g.alpha * __uint_as_float(v[4 * q + 3]));
+        return;
+    }
+    if (whole && g.c_vec == 2) {
+        // BF16, row-contiguous: two 16-byte vectors of 8 values
+        uint4* C4 = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.C) + off0);
+        uint4 old[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+        if (g.beta) {
+            old[0] = C4[0];
+            old[1] = C4[1];
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const uint32_t w[4] = {old[q].x, old[q].y, old[q].z, old[q].w};
+            uint32_t o[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const __nv_bfloat162 pw = *reinterpret_cast<const __nv_bfloat162*>(&w[i]);
+                const float lo = g.alpha * __uint_as_float(v[8 * q + 2 * i]) + (g.beta ? __low2float(pw) : 0.f);
+                const float hi = g.alpha * __uint_as_float(v[8 * q + 2 * i + 1]) + (g.beta ? __high2float(pw) : 0.f);
+                const __nv_bfloat162 r = __floats2bfloat162_rn(lo, hi);
+                o[i] = *reinterpret_cast<const uint32_t*>(&r);
             }
-            C4[q] = o;
+            C4[q] = make_uint4(o[0], o[1], o[2], o[3]);
         }
         return;
+    }
+    float old[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        old[j] = 0.f;
+        if (g.beta && n + j < g.N) {
+            const long long off = off0 + (long long)j * g.scn;
+            old[j] = g.out_bf16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(g.C)[off])
+                                : reinterpret_cast<const float*>(g.C)[off];
+        }
     }
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         if (n + j >= g.N) break;
-        const float val = g.alpha * __uint_as_float(v[j]);
+        const float val = g.alpha * __uint_as_float(v[j]) + old[j];
         const long long off = off0 + (long long)j * g.scn;
-        if (g.out_bf16) {
-            __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(g.C) + off;
-            *C = __float2bfloat16(g.beta ? __bfloat162float(*C) + val : val);
-        } else {
-            float* C = reinterpret_cast<float*>(g.C) + off;
-            *C = g.beta ? *C + val : val;
-        }
+        if (g.out_bf16)
+            reinterpret_cast<__nv_bfloat16*>(g.C)[off] = __float2bfloat16(val);
+        else
+            reinterpret_cast<float*>(g.C)[off] = val;
     }
 }
 
-template <int TN, int STAGES>
+template <int TN>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_bf16_tma(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, Args g) {
-    constexpr int B_STAGE = TN * TK * 2;
-    constexpr int STAGE = A_STAGE + B_STAGE;
+    constexpr int B_BLOCK = TN * TK * 2;    // one K block of B: TN rows x 64 K
     constexpr uint32_t TMEM_COLS = 2 * TN;  // two accumulators of 128 lanes x TN FP32 columns
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
+    __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES], tfull[2], tempty[2], drain, bres;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t ring = (smem_u32(smem_raw) + SMEM_ALIGN - 1) & ~(uint32_t)(SMEM_ALIGN - 1);
+    const uint32_t res = (smem_u32(smem_raw) + SMEM_ALIGN - 1) & ~(uint32_t)(SMEM_ALIGN - 1);
+    const uint32_t ring = res + (uint32_t)g.res_bytes;
+    const uint32_t stages = (uint32_t)g.stages, stage_bytes = (uint32_t)g.stage_bytes;
 
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
@@ -513,7 +554,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     if (tid == 0) {
         abort_flag = 0;
-        for (int s = 0; s < STAGES; ++s) {
+        for (uint32_t s = 0; s < stages; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[s])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[s])) : "memory");
         }
@@ -522,6 +563,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(&tempty[a])) : "memory");
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&drain)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bres)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
@@ -533,50 +575,72 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (warp == 0 && lane == 0) {
         // ---- TMA producer
-        uint32_t it = 0;
+        if (g.b_res) {
+            // the whole (shared) B once: K block kb at res + kb * B_BLOCK
+            const uint32_t bar = smem_u32(&bres);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
+                         "r"((uint32_t)(g.k_blocks * B_BLOCK))
+                         : "memory");
+            for (int kb = 0; kb < g.k_blocks; ++kb) {
+                const uint32_t sb = res + (uint32_t)(kb * B_BLOCK);
+                if (g.b_mn) {
+#pragma unroll
+                    for (int j = 0; j < TN / ATOM; ++j) tma_load(sb + j * ATOM * TK * 2, &map_b, j * ATOM, kb * TK, 0, false, bar);
+                } else {
+                    tma_load(sb, &map_b, kb * TK, 0, 0, false, bar);
+                }
+            }
+        }
+        uint32_t it = 0, s = 0, ph = 0;  // blocks issued; stage and the parity of its current use
         for (long long t = blockIdx.x; t < g.tiles && !abort_flag; t += gridDim.x) {
             int b, m0, tn;
             tile_coords(g, t, b, m0, tn);
             const int n0 = tn * TN;
-            for (int kb = 0; kb < g.k_blocks; ++kb, ++it) {
-                const uint32_t s = it % STAGES, use = it / STAGES;
-                if (!wait_or_abort(smem_u32(&empty[s]), (use & 1) ^ 1, &abort_flag)) {
+            for (int kb = 0; kb < g.k_blocks; ++kb, ++it, s = (s + 1 == stages) ? (ph ^= 1u, 0u) : s + 1) {
+                if (!wait_or_abort(smem_u32(&empty[s]), ph ^ 1, &abort_flag)) {
                     abort_flag = 1;
                     break;
                 }
                 const uint32_t bar = smem_u32(&full[s]);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(STAGE)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(stage_bytes)
                              : "memory");
-                const uint32_t sa = ring + s * STAGE, sb = sa + A_STAGE;
+                const uint32_t sa = ring + s * stage_bytes, sb = sa + (uint32_t)g.a_bytes;
                 const int k0 = kb * TK;
                 if (g.a_mn) {
                     // two 64-row atoms: rows m0 .. m0 + 127 of one item, or (packed) rows 0 .. 63 of
                     // items b and b + 1 in one box
                     tma_load(sa, &map_a, m0, k0, b, g.a_3d, bar);
-                    if (g.pack == 1) tma_load(sa + ATOM * TK * 2, &map_a, m0 + ATOM, k0, b, g.a_3d, bar);
+                    if (g.pack == 1) tma_load(sa + (uint32_t)(g.a_bytes / 2), &map_a, m0 + ATOM, k0, b, g.a_3d, bar);
                 } else {
                     tma_load(sa, &map_a, k0, m0, b, g.a_3d, bar);
                 }
-                if (g.b_mn) {
+                if (!g.b_res) {
+                    if (g.b_mn) {
 #pragma unroll
-                    for (int j = 0; j < TN / ATOM; ++j) tma_load(sb + j * ATOM * TK * 2, &map_b, n0 + j * ATOM, k0, b, g.b_3d, bar);
-                } else {
-                    tma_load(sb, &map_b, k0, n0, b, g.b_3d, bar);
+                        for (int j = 0; j < TN / ATOM; ++j)
+                            tma_load(sb + j * ATOM * TK * 2, &map_b, n0 + j * ATOM, k0, b, g.b_3d, bar);
+                    } else {
+                        tma_load(sb, &map_b, k0, n0, b, g.b_3d, bar);
+                    }
                 }
             }
         }
         // every copy issued has landed before the block can exit: wait for the last phase of each
-        // stage that was used (at once on a normal exit)
-        for (uint32_t s = 0; s < STAGES && s < it; ++s) {
-            const uint32_t last = it - 1 - ((it - 1 + STAGES - s) % STAGES);  // last iteration on stage s
-            volatile int never = 0;
-            if (!wait_or_abort(smem_u32(&full[last % STAGES]), (last / STAGES) & 1, &never)) atomicOr(g.err, 1u);
+        // stage that was used, and for the resident B (at once on a normal exit)
+        volatile int never = 0;
+        for (uint32_t j = 0; j < stages && j < it; ++j) {
+            const uint32_t last = it - 1 - ((it - 1 + stages - j) % stages);  // last block on stage j
+            if (!wait_or_abort(smem_u32(&full[j]), (last / stages) & 1, &never)) atomicOr(g.err, 1u);
         }
+        if (g.b_res && !wait_or_abort(smem_u32(&bres), 0, &never)) atomicOr(g.err, 1u);
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer
         const uint32_t idesc = instr_desc(TM, TN) | ((uint32_t)g.a_mn << 15) | ((uint32_t)g.b_mn << 16);
-        uint32_t it = 0, lt = 0;
-        for (long long t = blockIdx.x; t < g.tiles && !abort_flag; t += gridDim.x, ++lt) {
+        const uint32_t a_lbo = (uint32_t)(g.a_bytes / 2);  // M-major A: the second 64-row atom
+        bool ok = !g.b_res || wait_or_abort(smem_u32(&bres), 0, &abort_flag);
+        if (!ok) abort_flag = 1;
+        uint32_t s = 0, ph = 0, lt = 0;
+        for (long long t = blockIdx.x; ok && t < g.tiles && !abort_flag; t += gridDim.x, ++lt) {
             const uint32_t a = lt & 1, ause = lt >> 1;
             if (!wait_or_abort(smem_u32(&tempty[a]), (ause & 1) ^ 1, &abort_flag)) {
                 abort_flag = 1;
@@ -584,23 +648,21 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint32_t d = tmem + a * TN;
-            bool ok = true;
-            for (int kb = 0; kb < g.k_blocks; ++kb, ++it) {
-                const uint32_t s = it % STAGES, use = it / STAGES;
-                if (!wait_or_abort(smem_u32(&full[s]), use & 1, &abort_flag)) {
+            for (int kb = 0; kb < g.k_blocks; ++kb, s = (s + 1 == stages) ? (ph ^= 1u, 0u) : s + 1) {
+                if (!wait_or_abort(smem_u32(&full[s]), ph, &abort_flag)) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const uint32_t sa = ring + s * STAGE, sb = sa + A_STAGE;
+                const uint32_t sa = ring + s * stage_bytes;
+                const uint32_t sb = g.b_res ? res + (uint32_t)(kb * B_BLOCK) : sa + (uint32_t)g.a_bytes;
                 const int kmax = min(TK, ((g.K - kb * TK + 15) >> 4) << 4);
 #pragma unroll
                 for (int j = 0; j < TK / 16; ++j) {
                     if (16 * j >= kmax) break;  // zero padding past the end of K: no MMA
                     // K-major: the 16-deep step is 32 B further along each swizzled row; M/N-major:
-                    // 16 K rows = two 1024-byte groups further, atoms of 64 rows 8 KB apart
-                    const uint64_t ad = g.a_mn ? sw128_desc(sa + 2048u * j, ATOM * TK * 2, 1024)
-                                               : sw128_desc(sa + 32u * j, 16, 1024);
+                    // 16 K rows = two 1024-byte groups further, 64-row atoms LBO apart
+                    const uint64_t ad = g.a_mn ? sw128_desc(sa + 2048u * j, a_lbo, 1024) : sw128_desc(sa + 32u * j, 16, 1024);
                     const uint64_t bd = g.b_mn ? sw128_desc(sb + 2048u * j, ATOM * TK * 2, 1024)
                                                : sw128_desc(sb + 32u * j, 16, 1024);
                     const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
@@ -649,17 +711,17 @@ __global__ void __launch_bounds__(THREADS, 1)
             const bool live = row < g.M && item < g.batch;
             const long long rowoff = (long long)item * g.scb + (long long)row * g.scm;
             const int ncols = min(TN, g.N - n0);
-            for (int c0 = 0; c0 < ncols; c0 += 64) {
-                // up to four 16-column loads in flight, then one wait
-                uint32_t v[4][16];
+            for (int c0 = 0; c0 < ncols; c0 += 32) {
+                // two 16-column loads in flight, then one wait
+                uint32_t v[2][16];
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * TN + (uint32_t)c0;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < 2; ++j)
                     if (c0 + 16 * j < ncols) tmem_ld16(taddr + 16 * j, v[j]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                 if (live) {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
+                    for (int j = 0; j < 2; ++j)
                         if (c0 + 16 * j < ncols) {
                             const int n = n0 + c0 + 16 * j;
                             store16(g, rowoff + (long long)n * g.scn, n, v[j]);
@@ -734,11 +796,11 @@ EncodeTiled encoder() {
 // Tensor map of an operand whose element (r, k) of batch item b sits at base + r sr + k sk + b sb
 // (elements), r < R, k < K.  A K-contiguous operand (sk = 1) is described K-fastest with boxes of
 // 64 K x box_rows rows x box_items items; an R-contiguous one (sr = 1) R-fastest with boxes of 64
-// rows x 64 K x box_items items.  Both use the 128-byte swizzle.  Returns false when the copy engine
+// rows x box_k K x box_items items.  Both use the 128-byte swizzle.  Returns false when the copy engine
 // cannot address the operand: base not 16-byte aligned, a stride that is not a positive multiple
 // of 8 elements, no unit stride.
 bool operand_map(CUtensorMap* map, const void* base, int R, int K, int batch, long long sr, long long sk, long long sb,
-                 int box_rows, int box_items, int* mn_major, int* three) {
+                 int box_rows, int box_items, int box_k, int* mn_major, int* three) {
     const EncodeTiled enc = encoder();
     if (!enc || !aligned16(base)) return false;
     cuuint64_t dims[3], strides[2];
@@ -756,7 +818,7 @@ bool operand_map(CUtensorMap* map, const void* base, int R, int K, int batch, lo
         dims[1] = (cuuint64_t)K;
         strides[0] = (cuuint64_t)sk * 2;
         box[0] = tma::ATOM;
-        box[1] = TK;
+        box[1] = (cuuint32_t)box_k;
     } else {
         return false;
     }
@@ -782,21 +844,18 @@ int sm_count() {
     return n > 0 ? n : 1;
 }
 
-template <int TN, int STAGES>
-cudaError_t launch_tma_tn(const CUtensorMap& ma, const CUtensorMap& mb, tma::Args a, int batch, cudaStream_t st) {
-    constexpr int smem = STAGES * (tma::A_STAGE + TN * TK * 2) + tma::SMEM_ALIGN + tma::SMEM_TAIL;
+template <int TN>
+cudaError_t launch_tma_tn(const CUtensorMap& ma, const CUtensorMap& mb, tma::Args a, cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
         const cudaError_t e =
-            cudaFuncSetAttribute(tma::k_gemm_bf16_tma<TN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaFuncSetAttribute(tma::k_gemm_bf16_tma<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tma::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    a.tiles_n = (a.N + TN - 1) / TN;
-    a.tiles = (long long)a.tiles_m * a.tiles_n * ((batch + a.pack - 1) / a.pack);
     static const int sms = sm_count();
     const long long grid = a.tiles < sms ? a.tiles : sms;
-    tma::k_gemm_bf16_tma<TN, STAGES><<<(unsigned)grid, tma::THREADS, smem, st>>>(ma, mb, a);
+    tma::k_gemm_bf16_tma<TN><<<(unsigned)grid, tma::THREADS, tma::SMEM_BYTES, st>>>(ma, mb, a);
     return cudaGetLastError();
 }
 
@@ -808,15 +867,31 @@ bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* 
     tma::Args a;
     // items of at most 64 rows against one shared B: two per 128-row tile
     a.pack = (g.M <= tma::ATOM && batch > 1 && g.sbb == 0 && g.sab != 0) ? 2 : 1;
-    if (!operand_map(&ma, g.A, g.M, g.K, batch, g.sam, g.sak, g.sab, TM / a.pack, a.pack, &a.a_mn, &a.a_3d))
+    // an M-major A box only as deep in K as a short K needs (rounded up to the MMA depth)
+    const int kbox = g.K < TK ? ((g.K + 15) >> 4) << 4 : TK;
+    const bool a_mn_layout = !(g.sak == 1 && g.sam > 0 && g.sam % 8 == 0);
+    if (!operand_map(&ma, g.A, g.M, g.K, batch, g.sam, g.sak, g.sab, TM / a.pack, a.pack, a_mn_layout ? kbox : TK,
+                     &a.a_mn, &a.a_3d))
         return false;
-    if (!operand_map(&mb, g.B, g.N, g.K, batch, g.sbn, g.sbk, g.sbb, TN, 1, &a.b_mn, &a.b_3d)) return false;
+    if (!operand_map(&mb, g.B, g.N, g.K, batch, g.sbn, g.sbk, g.sbb, TN, 1, TK, &a.b_mn, &a.b_3d)) return false;
     a.M = g.M;
     a.N = g.N;
     a.K = g.K;
     a.batch = batch;
     a.tiles_m = (g.M + TM - 1) / TM;
+    a.tiles_n = (g.N + TN - 1) / TN;
     a.k_blocks = (g.K + TK - 1) / TK;
+    a.tiles = (long long)a.tiles_m * a.tiles_n * ((batch + a.pack - 1) / a.pack);
+    a.a_kbox = a.a_mn ? kbox : TK;
+    a.a_bytes = a.a_mn ? 2 * tma::ATOM * a.a_kbox * 2 : TM * TK * 2;
+    const int b_block = TN * TK * 2;
+    // one B for every tile (shared by the batch, one column tile) that fits in half the budget
+    a.b_res = !a.b_3d && a.tiles_n == 1 && (long long)a.k_blocks * b_block <= tma::SMEM_USE / 2;
+    a.res_bytes = a.b_res ? a.k_blocks * b_block : 0;
+    a.stage_bytes = a.a_bytes + (a.b_res ? 0 : b_block);
+    a.stages = (tma::SMEM_USE - a.res_bytes) / a.stage_bytes;
+    if (a.stages > tma::MAX_STAGES) a.stages = tma::MAX_STAGES;
+    if (a.stages < 2) return false;
     a.C = g.C;
     a.scm = g.scm;
     a.scn = g.scn;
@@ -827,11 +902,11 @@ bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* 
     a.c_vec = g.c_vec;
     a.err = g.err;
     if (TN == 64)
-        *err = launch_tma_tn<64, 8>(ma, mb, a, batch, st);
+        *err = launch_tma_tn<64>(ma, mb, a, st);
     else if (TN == 128)
-        *err = launch_tma_tn<128, 6>(ma, mb, a, batch, st);
+        *err = launch_tma_tn<128>(ma, mb, a, st);
     else
-        *err = launch_tma_tn<256, 4>(ma, mb, a, batch, st);
+        *err = launch_tma_tn<256>(ma, mb, a, st);
     return true;
 }
 
@@ -840,7 +915,9 @@ bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* 
 cudaError_t launch_gemm_bf16(const GemmArgs& g_in, int batch, cudaStream_t st) {
     if (g_in.M <= 0 || g_in.N <= 0 || g_in.K < 0 || batch <= 0) return cudaErrorInvalidValue;
     GemmArgs g = g_in;
-    g.c_vec = !g.out_bf16 && g.scn == 1 && g.scm % 4 == 0 && (batch == 1 || g.scb % 4 == 0) && aligned16(g.C);
+    // C stored as 16-byte vectors: 1 FP32 (4 per vector), 2 BF16 (8 per vector), 0 element by element
+    const int per = g.out_bf16 ? 8 : 4;
+    g.c_vec = (g.scn == 1 && g.scm % per == 0 && (batch == 1 || g.scb % per == 0) && aligned16(g.C)) ? (g.out_bf16 ? 2 : 1) : 0;
     cudaError_t e = cudaSuccess;
     if (try_launch_tma(g, batch, st, &e)) return e;
     g.a_mode = stage_mode(g.A, g.sam, g.sak, g.sab, batch);

@@ -24,9 +24,9 @@ struct GemmArgs {
     float alpha;
     int beta;
     unsigned int* err;
-    // set by launch_gemm_bf16 from the strides and alignment: staging mode of A and B (0 element
-    // by element, 1 K-contiguous 16-byte rows, 2 row-contiguous 8 x 8 blocks), C stored as
-    // 16-byte vectors
+    // set by launch_gemm_bf16 from the strides and alignment: staging mode of A and B in the
+    // register-staged kernel (0 element by element, 1 K-contiguous 16-byte rows, 2 row-contiguous
+    // 8 x 8 blocks); C stored as 16-byte vectors (1 FP32, 2 BF16) or element by element (0)
     int a_mode, b_mode, c_vec;
 };
 

@@ -133,22 +133,30 @@ def test_gemm_tma_operand_layouts(a_k, b_k, M, N, K, nb, b_shared):
 
 
 @pytest.mark.parametrize("out_bf16", [0, 1])
-def test_gemm_tma_alpha_beta_column_major_c(out_bf16):
-    """The copy-engine path's epilogue: C column-major (M contiguous), alpha = -0.75, added to the
-    previous C (beta), FP32 or BF16 output."""
+@pytest.mark.parametrize("c_row_major", [False, True])
+def test_gemm_tma_alpha_beta_epilogue(out_bf16, c_row_major):
+    """The copy-engine path's epilogue: alpha = -0.75 added to the previous C (beta), FP32 or BF16
+    output, C column-major (M contiguous: element by element) or row-major (N contiguous: 16-byte
+    vectors, with a ragged last column chunk)."""
     M, N, K, nb = 260, 72, 96, 2
-    rng = np.random.default_rng(77 + out_bf16)
+    rng = np.random.default_rng(77 + out_bf16 + 2 * c_row_major)
     a, Ad, sa = _operand(rng, M, K, nb, True, 0)
     b, Bd, sbt = _operand(rng, N, K, nb, False, 8)
     sb = (sbt[1], sbt[0], sbt[2])
-    c0 = rng.normal(size=(nb, N, M)).astype(np.float32)                 # C[b][m][n] at (b, n, m)
     dt = torch.bfloat16 if out_bf16 else torch.float32
+    if c_row_major:
+        c0 = rng.normal(size=(nb, M, N)).astype(np.float32)            # C[b][m][n] at (b, m, n)
+        sc = (N, 1, M * N)
+    else:
+        c0 = rng.normal(size=(nb, N, M)).astype(np.float32)            # C[b][m][n] at (b, n, m)
+        sc = (1, M, N * M)
     C = torch.from_numpy(c0).to(dt).cuda()
     c0 = C.float().cpu().numpy().astype(np.float64)
-    _gemm(M, N, K, nb, Ad, sa, Bd, sb, C, (1, M, N * M), out_bf16=out_bf16, alpha=-0.75, beta=1)
-    prod = np.einsum("imk,ink->inm", a, b)
+    _gemm(M, N, K, nb, Ad, sa, Bd, sb, C, sc, out_bf16=out_bf16, alpha=-0.75, beta=1)
+    eq = "imk,ink->imn" if c_row_major else "imk,ink->inm"
+    prod = np.einsum(eq, a, b)
     ref = c0 - 0.75 * prod
-    bound = 0.75 * 2.0 ** -20 * np.einsum("imk,ink->inm", np.abs(a), np.abs(b))
+    bound = 0.75 * 2.0 ** -20 * np.einsum(eq, np.abs(a), np.abs(b))
     if out_bf16:
         bound = bound + 2.0 ** -8 * np.abs(ref)
     _check(C.float().cpu().numpy(), ref, bound)
