@@ -115,6 +115,11 @@ __global__ void k_act_bwd(const float* __restrict__ dh, const float* __restrict_
 // numbers.  The mean's mode is added back in FP32 (k_add_dc).  Three passes: partial sums over
 // CENTER_PARTS chunks per channel (FP32 per thread, FP64 per block), the means in a fixed order,
 // then the element-wise centring.
+__device__ __forceinline__ uint2 pack_bf16x4(float4 v) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+}
+
 constexpr int CENTER_PARTS = 16;
 
 __global__ void __launch_bounds__(256) k_center_partials(const float* __restrict__ src, long long S, int use_gelu,
@@ -127,6 +132,40 @@ __global__ void __launch_bounds__(256) k_center_partials(const float* __restrict
     for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const float v = x[i];
         acc += use_gelu ? gelu(v) : v;
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// The same partition, four values per load (S a multiple of 4, rows 16-byte aligned): part p of
+// a row covers the float4 groups [p per4, (p + 1) per4).
+__global__ void __launch_bounds__(256) k_center_partials_v(const float* __restrict__ src, long long S, int use_gelu,
+                                                           double* __restrict__ part) {
+    const int bc = blockIdx.x / CENTER_PARTS, p = blockIdx.x % CENTER_PARTS;
+    const long long S4 = S / 4, per = (S4 + CENTER_PARTS - 1) / CENTER_PARTS;
+    const long long lo = p * per, hi = lo + per < S4 ? lo + per : S4;
+    const float4* x = reinterpret_cast<const float4*>(src + (long long)bc * S);
+    float acc = 0.0f;
+#pragma unroll 4
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const float4 v = __ldg(x + i);
+        if (use_gelu) {
+            acc += gelu(v.x);
+            acc += gelu(v.y);
+            acc += gelu(v.z);
+            acc += gelu(v.w);
+        } else {
+            acc += v.x;
+            acc += v.y;
+            acc += v.z;
+            acc += v.w;
+        }
     }
     __shared__ double sh[256];
     sh[threadIdx.x] = acc;
@@ -157,6 +196,20 @@ __global__ void k_center_apply(const float* __restrict__ src, long long S, int u
     }
 }
 
+__global__ void __launch_bounds__(256) k_center_apply_v(const float* __restrict__ src, long long S, int use_gelu,
+                                                        const float* __restrict__ mean, bf16* __restrict__ out) {
+    const long long base = (long long)blockIdx.y * S;
+    const float m = mean[blockIdx.y];
+    const float4* x = reinterpret_cast<const float4*>(src + base);
+    uint2* o = reinterpret_cast<uint2*>(out + base);
+#pragma unroll 4
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S / 4; i += (long long)gridDim.x * blockDim.x) {
+        float4 v = __ldg(x + i);
+        if (use_gelu) v = make_float4(gelu(v.x), gelu(v.y), gelu(v.z), gelu(v.w));
+        o[i] = pack_bf16x4(make_float4(v.x - m, v.y - m, v.z - m, v.w - m));
+    }
+}
+
 // Mode (0, 0, 0), real part, of each (sample, channel) row block of a mode array laid out
 // [b][c][kx][ky][ri][kz]: += scale * mean[b * W + c].
 __global__ void k_add_dc(float* __restrict__ modes, const float* __restrict__ mean, int rows, long long stride,
@@ -184,6 +237,68 @@ __global__ void k_permute6(const bf16* __restrict__ in, bf16* __restrict__ out, 
             off += ij * sin[P.perm[j]];
         }
         out[idx] = in[off];
+    }
+}
+
+// The two permutations between the y and z transforms, per (b, c) slab: [z][kx][ri][ky] <->
+// [kx][ky][ri][z].  One block per (b c, kx) moves the D x 2 MY sub-slab of that kx through shared
+// memory (rows padded by two elements against bank conflicts), reading and writing 16-byte
+// vectors; needs D and 2 MY multiples of 8 and 16-byte aligned buffers.
+__global__ void __launch_bounds__(256) k_to_zlast(const bf16* __restrict__ in, bf16* __restrict__ out, int D, int MX,
+                                                  int MY) {
+    extern __shared__ bf16 sm[];  // [z][ri * MY + ky]
+    const int L = 2 * MY, R = L + 2;
+    const long long bc = blockIdx.x / MX;
+    const int kx = blockIdx.x % MX;
+    const bf16* src = in + (bc * D * MX + kx) * L;  // row z at src + z MX L
+    const int nv = L / 8;
+    for (int e = threadIdx.x; e < D * nv; e += blockDim.x) {
+        const int z = e / nv, v = e % nv;
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(src + (long long)z * MX * L + v * 8));
+        const bf16* h = reinterpret_cast<const bf16*>(&q);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sm[z * R + v * 8 + k] = h[k];
+    }
+    __syncthreads();
+    bf16* dst = out + (bc * MX + kx) * (long long)L * D;  // element (ky 2 + ri) D + z
+    const int nz = D / 8;
+    for (int e = threadIdx.x; e < L * nz; e += blockDim.x) {
+        const int qd = e / nz, z0 = (e % nz) * 8;
+        const int ky = qd >> 1, ri = qd & 1;
+        __align__(16) bf16 h[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h[k] = sm[(z0 + k) * R + ri * MY + ky];
+        *reinterpret_cast<uint4*>(dst + (long long)qd * D + z0) = *reinterpret_cast<const uint4*>(h);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_from_zlast(const bf16* __restrict__ in, bf16* __restrict__ out, int D, int MX,
+                                                    int MY) {
+    extern __shared__ bf16 sm[];  // [ky 2 + ri][z]
+    const int L = 2 * MY, R = D + 2;
+    const long long bc = blockIdx.x / MX;
+    const int kx = blockIdx.x % MX;
+    const bf16* src = in + (bc * MX + kx) * (long long)L * D;
+    const int nz = D / 8;
+    for (int e = threadIdx.x; e < L * nz; e += blockDim.x) {
+        const int qd = e / nz, z0 = (e % nz) * 8;
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(src + (long long)qd * D + z0));
+        const bf16* h = reinterpret_cast<const bf16*>(&q);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sm[qd * R + z0 + k] = h[k];
+    }
+    __syncthreads();
+    bf16* dst = out + (bc * D * MX + kx) * L;  // row z at dst + z MX L, element ri MY + ky
+    const int nv = L / 8;
+    for (int e = threadIdx.x; e < D * nv; e += blockDim.x) {
+        const int z = e / nv, j0 = (e % nv) * 8;
+        __align__(16) bf16 h[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int j = j0 + k, ri = j / MY, ky = j - ri * MY;
+            h[k] = sm[(ky * 2 + ri) * R + z];
+        }
+        *reinterpret_cast<uint4*>(dst + (long long)z * MX * L + j0) = *reinterpret_cast<const uint4*>(h);
     }
 }
 
@@ -298,6 +413,166 @@ __global__ void __launch_bounds__(256) k_mix_bwd_w(const float* __restrict__ dY,
         }
 }
 
+// Width-32 forms of the three mixing kernels, the operator's configuration.  One warp per mode; a
+// mode's 32 x 32 complex matrix is 8 KB contiguous ([o][c][ri]).  Each lane holds one row (forward:
+// lane = o, sixteen 16-byte loads issued together) or one column (input gradient: lane = c, 32
+// loads of 8 bytes, each a coalesced 256-byte row of the warp) of it in registers, and the mode's
+// coefficients of the other index are staged per warp in shared memory ([channel][sample][ri],
+// read back as broadcasts), four samples at a time.  Every output is summed over the channel (or
+// the sample) in the same order as the general kernels.
+constexpr int MIX_W = 32, MIX_S = 4;
+
+// the warp's shared buffer <- v[b0 + j][ch = lane][kx][ky][ri][kz], j < MIX_S (zeros past nb)
+__device__ __forceinline__ void stage_mode(const float* __restrict__ V, const MixDims& d, int b0, int nb, int kx, int ky,
+                                           int kz, float* sv, int lane) {
+    float t[2 * MIX_S];
+#pragma unroll
+    for (int j = 0; j < MIX_S; ++j) {
+        t[2 * j] = j < nb ? V[xidx(d, b0 + j, lane, kx, ky, 0, kz)] : 0.0f;
+        t[2 * j + 1] = j < nb ? V[xidx(d, b0 + j, lane, kx, ky, 1, kz)] : 0.0f;
+    }
+    float4* dst = reinterpret_cast<float4*>(sv + lane * 2 * MIX_S);
+    dst[0] = make_float4(t[0], t[1], t[2], t[3]);
+    dst[1] = make_float4(t[4], t[5], t[6], t[7]);
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(256) k_mix_fwd32(const float* __restrict__ X, const float* __restrict__ Wm, MixDims d,
+                                                   bf16* __restrict__ Y) {
+    __shared__ __align__(16) float sbuf[8][MIX_W * 2 * MIX_S];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long m = (long long)blockIdx.x * 8 + warp;
+    if (m >= (long long)d.MX * d.MY * d.MZ) return;
+    int kx, ky, kz;
+    mode_of(d, m, kx, ky, kz);
+    const float4* w4 = reinterpret_cast<const float4*>(Wm + widx(d, kx, ky, kz, lane, 0));
+    float4 w[MIX_W / 2];  // row o = lane: w[i] = (re, im) of c = 2i, 2i + 1
+#pragma unroll
+    for (int i = 0; i < MIX_W / 2; ++i) w[i] = __ldg(w4 + i);
+    float* sv = sbuf[warp];
+    for (int b0 = 0; b0 < d.B; b0 += MIX_S) {
+        const int nb = min(MIX_S, d.B - b0);
+        stage_mode(X, d, b0, nb, kx, ky, kz, sv, lane);
+        float yr[MIX_S], yi[MIX_S];
+#pragma unroll
+        for (int j = 0; j < MIX_S; ++j) yr[j] = yi[j] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < MIX_W; ++c) {
+            const float wr = (c & 1) ? w[c >> 1].z : w[c >> 1].x, wi = (c & 1) ? w[c >> 1].w : w[c >> 1].y;
+            const float4 x01 = *reinterpret_cast<const float4*>(sv + c * 2 * MIX_S);
+            const float4 x23 = *reinterpret_cast<const float4*>(sv + c * 2 * MIX_S + 4);
+            const float xr[MIX_S] = {x01.x, x01.z, x23.x, x23.z}, xi[MIX_S] = {x01.y, x01.w, x23.y, x23.w};
+#pragma unroll
+            for (int j = 0; j < MIX_S; ++j) {
+                yr[j] += wr * xr[j] - wi * xi[j];
+                yi[j] += wr * xi[j] + wi * xr[j];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < MIX_S; ++j)
+            if (j < nb) {
+                Y[xidx(d, b0 + j, lane, kx, ky, 0, kz)] = __float2bfloat16(yr[j]);
+                Y[xidx(d, b0 + j, lane, kx, ky, 1, kz)] = __float2bfloat16(yi[j]);
+            }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mix_bwd_x32(const float* __restrict__ dY, const float* __restrict__ Wm,
+                                                     MixDims d, bf16* __restrict__ dX) {
+    __shared__ __align__(16) float sbuf[8][MIX_W * 2 * MIX_S];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long m = (long long)blockIdx.x * 8 + warp;
+    if (m >= (long long)d.MX * d.MY * d.MZ) return;
+    int kx, ky, kz;
+    mode_of(d, m, kx, ky, kz);
+    const float2* w2 = reinterpret_cast<const float2*>(Wm + widx(d, kx, ky, kz, 0, lane));
+    float2 w[MIX_W];  // column c = lane: w[o] = W[o][c]
+#pragma unroll
+    for (int o = 0; o < MIX_W; ++o) w[o] = __ldg(w2 + o * MIX_W);
+    float* sv = sbuf[warp];
+    for (int b0 = 0; b0 < d.B; b0 += MIX_S) {
+        const int nb = min(MIX_S, d.B - b0);
+        stage_mode(dY, d, b0, nb, kx, ky, kz, sv, lane);
+        float xr[MIX_S], xi[MIX_S];
+#pragma unroll
+        for (int j = 0; j < MIX_S; ++j) xr[j] = xi[j] = 0.0f;
+#pragma unroll
+        for (int o = 0; o < MIX_W; ++o) {
+            const float wr = w[o].x, wi = w[o].y;
+            const float4 y01 = *reinterpret_cast<const float4*>(sv + o * 2 * MIX_S);
+            const float4 y23 = *reinterpret_cast<const float4*>(sv + o * 2 * MIX_S + 4);
+            const float yr[MIX_S] = {y01.x, y01.z, y23.x, y23.z}, yi[MIX_S] = {y01.y, y01.w, y23.y, y23.w};
+#pragma unroll
+            for (int j = 0; j < MIX_S; ++j) {
+                xr[j] += wr * yr[j] + wi * yi[j];
+                xi[j] += -wi * yr[j] + wr * yi[j];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < MIX_S; ++j)
+            if (j < nb) {
+                dX[xidx(d, b0 + j, lane, kx, ky, 0, kz)] = __float2bfloat16(xr[j]);
+                dX[xidx(d, b0 + j, lane, kx, ky, 1, kz)] = __float2bfloat16(xi[j]);
+            }
+    }
+}
+
+// dW[o][c] (+)= sum_b dY[b][o] conj(X[b][c]) for B <= MIX_SB samples, lane = c: X of the lane's
+// channel in registers, every sample's dY staged; each o a coalesced 256-byte row of the warp.
+// `add`: accumulate onto dW, else overwrite.
+constexpr int MIX_SB = 16;
+
+__global__ void __launch_bounds__(256) k_mix_bwd_w32(const float* __restrict__ dY, const float* __restrict__ X, MixDims d,
+                                                     float* __restrict__ dW, int add) {
+    __shared__ __align__(16) float sbuf[8][MIX_W * 2 * MIX_SB];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long m = (long long)blockIdx.x * 8 + warp;
+    if (m >= (long long)d.MX * d.MY * d.MZ) return;
+    int kx, ky, kz;
+    mode_of(d, m, kx, ky, kz);
+    float xr[MIX_SB], xi[MIX_SB];
+    float* sv = sbuf[warp];
+#pragma unroll
+    for (int j = 0; j < MIX_SB; ++j) {
+        xr[j] = j < d.B ? X[xidx(d, j, lane, kx, ky, 0, kz)] : 0.0f;
+        xi[j] = j < d.B ? X[xidx(d, j, lane, kx, ky, 1, kz)] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < MIX_SB; j += 2)
+        if (j < d.B) {
+            const bool two = j + 1 < d.B;
+            *reinterpret_cast<float4*>(sv + (lane * MIX_SB + j) * 2) =
+                make_float4(dY[xidx(d, j, lane, kx, ky, 0, kz)], dY[xidx(d, j, lane, kx, ky, 1, kz)],
+                            two ? dY[xidx(d, j + 1, lane, kx, ky, 0, kz)] : 0.0f, two ? dY[xidx(d, j + 1, lane, kx, ky, 1, kz)] : 0.0f);
+        }
+    __syncwarp();
+    float2* w2 = reinterpret_cast<float2*>(dW + widx(d, kx, ky, kz, 0, lane));
+#pragma unroll 4
+    for (int o = 0; o < MIX_W; ++o) {
+        float gr = 0.0f, gi = 0.0f;
+#pragma unroll
+        for (int j = 0; j < MIX_SB; j += 2)
+            if (j < d.B) {
+                const float4 y = *reinterpret_cast<const float4*>(sv + (o * MIX_SB + j) * 2);
+                gr += y.x * xr[j] + y.y * xi[j];
+                gi += -y.x * xi[j] + y.y * xr[j];
+                if (j + 1 < d.B) {
+                    gr += y.z * xr[j + 1] + y.w * xi[j + 1];
+                    gi += -y.z * xi[j + 1] + y.w * xr[j + 1];
+                }
+            }
+        float2 v = make_float2(gr, gi);
+        if (add) {
+            const float2 p = w2[o * MIX_W];
+            v.x += p.x;
+            v.y += p.y;
+        }
+        w2[o * MIX_W] = v;
+    }
+}
+
 // One chunk of the B * S positions per block, one (i, j) pair per group of blocks:
 // part[chunk][i * Cy + j] = sum over the chunk of X[b][i][s] * Y[b][j][s] (X alone if Y is null).
 // FP32 per thread (a few hundred terms at most), FP64 across the block; the chunks are summed in a
@@ -331,12 +606,24 @@ __global__ void k_reduce_bs(const float* __restrict__ X, const float* __restrict
 }
 
 // sum of partial blocks: out[k] += sum_p part[p][k]
-__global__ void k_sum_partials(const float* __restrict__ part, int P, int K, float* __restrict__ out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
+// out[k] += sum_p part[p][k]: a block takes 32 consecutive k (lanes) and splits the partials among
+// its 16 warps (warp w: p = w, w + 16, ...); the warps' sums are then added in warp order.
+__global__ void __launch_bounds__(512) k_sum_partials(const float* __restrict__ part, int P, int K, float* __restrict__ out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int k = blockIdx.x * 32 + lane;
     float a = 0.0f;
-    for (int p = 0; p < P; ++p) a += part[(long long)p * K + k];
-    out[k] += a;
+    if (k < K) {
+#pragma unroll 4
+        for (int p = warp; p < P; p += nw) a += part[(long long)p * K + k];
+    }
+    __shared__ float sh[16][32];
+    sh[warp][lane] = a;
+    __syncthreads();
+    if (warp == 0 && k < K) {
+        float t = 0.0f;
+        for (int w = 0; w < nw; ++w) t += sh[w][lane];
+        out[k] += t;
+    }
 }
 
 // mean squared error over all elements; dout = 2 (out - t) / n; loss accumulated in FP64
@@ -375,6 +662,110 @@ inline unsigned grid_for(long long n, int threads = 256) {
     if (b > 152LL * 32) b = 152LL * 32;
     if (b < 1) b = 1;
     return (unsigned)b;
+}
+
+// ---- row-vectorised forms of the pointwise maps (S a multiple of 4, buffers 16-byte aligned):
+// a thread takes four consecutive positions of one sample; channel loops run over registers.
+constexpr int VEC_CH = 8;  // input channels of the lift / output channels of the projection held in registers
+
+inline dim3 grid_rows(long long S, long long rows) { return dim3((unsigned)((S / 4 + 255) / 256), (unsigned)rows); }
+
+
+// z[b][o][s] += bias[o]; hb = act(z) (BF16); grid (positions / 1024, B W)
+__global__ void __launch_bounds__(256) k_bias_act_v(float* __restrict__ z, const float* __restrict__ bias, int W, long long S,
+                                                    int use_gelu, bf16* __restrict__ hb) {
+    const long long s4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s4 * 4 >= S) return;
+    const long long row = blockIdx.y;
+    const float bo = bias[row % W];
+    float4* zp = reinterpret_cast<float4*>(z + row * S) + s4;
+    float4 v = *zp;
+    v.x += bo;
+    v.y += bo;
+    v.z += bo;
+    v.w += bo;
+    *zp = v;
+    if (use_gelu) v = make_float4(gelu(v.x), gelu(v.y), gelu(v.z), gelu(v.w));
+    reinterpret_cast<uint2*>(hb + row * S)[s4] = pack_bf16x4(v);
+}
+
+// h[b][c][s] = p[c] + sum_i P[c][i] a[b][i][s] (Ci <= VEC_CH), h also as BF16; grid (positions / 1024, B)
+__global__ void __launch_bounds__(256) k_lift_v(const float* __restrict__ a, const float* __restrict__ P, const float* __restrict__ p,
+                                                int Ci, int W, long long S, float* __restrict__ h, bf16* __restrict__ hb) {
+    const long long s4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s4 * 4 >= S) return;
+    const long long b = blockIdx.y;
+    float4 x[VEC_CH];
+#pragma unroll
+    for (int i = 0; i < VEC_CH; ++i)
+        if (i < Ci) x[i] = __ldg(reinterpret_cast<const float4*>(a + (b * Ci + i) * S) + s4);
+    for (int c = 0; c < W; ++c) {
+        const float pc = p[c];
+        float4 v = make_float4(pc, pc, pc, pc);
+#pragma unroll
+        for (int i = 0; i < VEC_CH; ++i)
+            if (i < Ci) {
+                const float w = P[c * Ci + i];
+                v.x += w * x[i].x;
+                v.y += w * x[i].y;
+                v.z += w * x[i].z;
+                v.w += w * x[i].w;
+            }
+        reinterpret_cast<float4*>(h + (b * W + c) * S)[s4] = v;
+        reinterpret_cast<uint2*>(hb + (b * W + c) * S)[s4] = pack_bf16x4(v);
+    }
+}
+
+// out[b][k][s] = q[k] + sum_c Q[k][c] h[b][c][s] (Co <= VEC_CH); grid (positions / 1024, B)
+__global__ void __launch_bounds__(256) k_project_v(const float* __restrict__ h, const float* __restrict__ Q, const float* __restrict__ q,
+                                                   int W, int Co, long long S, float* __restrict__ out) {
+    const long long s4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s4 * 4 >= S) return;
+    const long long b = blockIdx.y;
+    float4 v[VEC_CH];
+#pragma unroll
+    for (int k = 0; k < VEC_CH; ++k)
+        if (k < Co) v[k] = make_float4(q[k], q[k], q[k], q[k]);
+    for (int c = 0; c < W; ++c) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(h + (b * W + c) * S) + s4);
+#pragma unroll
+        for (int k = 0; k < VEC_CH; ++k)
+            if (k < Co) {
+                const float w = Q[k * W + c];
+                v[k].x += w * x.x;
+                v[k].y += w * x.y;
+                v[k].z += w * x.z;
+                v[k].w += w * x.w;
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < VEC_CH; ++k)
+        if (k < Co) reinterpret_cast<float4*>(out + (b * Co + k) * S)[s4] = v[k];
+}
+
+// dh[b][c][s] = sum_k Q[k][c] dout[b][k][s] (Co <= VEC_CH); grid (positions / 1024, B)
+__global__ void __launch_bounds__(256) k_project_bwd_x_v(const float* __restrict__ dout, const float* __restrict__ Q, int W, int Co,
+                                                         long long S, float* __restrict__ dh) {
+    const long long s4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s4 * 4 >= S) return;
+    const long long b = blockIdx.y;
+    float4 g[VEC_CH];
+#pragma unroll
+    for (int k = 0; k < VEC_CH; ++k)
+        if (k < Co) g[k] = __ldg(reinterpret_cast<const float4*>(dout + (b * Co + k) * S) + s4);
+    for (int c = 0; c < W; ++c) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < VEC_CH; ++k)
+            if (k < Co) {
+                const float w = Q[k * W + c];
+                v.x += w * g[k].x;
+                v.y += w * g[k].y;
+                v.z += w * g[k].z;
+                v.w += w * g[k].w;
+            }
+        reinterpret_cast<float4*>(dh + (b * W + c) * S)[s4] = v;
+    }
 }
 
 uint64_t splitmix(uint64_t& s) {
@@ -472,6 +863,23 @@ cudaError_t gemm(lbm_no* n, int M, int N, int K, int batch, const bf16* A, long 
 }
 
 cudaError_t permute(lbm_no* n, const bf16* in, bf16* out, const long long din[6], const int perm[6]) {
+    // the transform boundary's two forms, through shared memory
+    const int D = n->D, MX = n->MX, MY = n->MY;
+    const bool vec = D % 8 == 0 && (2 * MY) % 8 == 0 && ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
+    const long long bcx = (long long)n->B * n->W * MX;
+    const bool to_z = din[2] == D && din[3] == MX && din[4] == 2 && din[5] == MY && perm[2] == 3 && perm[3] == 5 &&
+                      perm[4] == 4 && perm[5] == 2;
+    const bool from_z = din[2] == MX && din[3] == MY && din[4] == 2 && din[5] == D && perm[2] == 5 && perm[3] == 2 &&
+                        perm[4] == 4 && perm[5] == 3;
+    const size_t smem = (size_t)D * (2 * MY + 2) * sizeof(bf16) + (size_t)2 * MY * 2 * sizeof(bf16);
+    if (vec && din[0] * din[1] * MX == bcx && perm[0] == 0 && perm[1] == 1 && (to_z || from_z) && bcx < (1LL << 31) &&
+        smem <= 48 * 1024) {
+        if (to_z)
+            k_to_zlast<<<(unsigned)bcx, 256, smem, n->stream>>>(in, out, D, MX, MY);
+        else
+            k_from_zlast<<<(unsigned)bcx, 256, smem, n->stream>>>(in, out, D, MX, MY);
+        return cudaGetLastError();
+    }
     Perm6 P;
     long long total = 1;
     for (int a = 0; a < 6; ++a) {
@@ -488,17 +896,102 @@ constexpr int REDUCE_CHUNKS = 64;  // chunks of the B * S positions in a gradien
 // hs = bf16(act(src) - mean), hmean = the per-(sample, channel) means (see k_center_partials)
 cudaError_t center(lbm_no* n, const float* src, int use_gelu) {
     const int ch = n->B * n->W;
-    k_center_partials<<<ch * CENTER_PARTS, 256, 0, n->stream>>>(src, n->S, use_gelu, n->cpart);
+    const bool v4 = n->S % 4 == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+    if (v4)
+        k_center_partials_v<<<ch * CENTER_PARTS, 256, 0, n->stream>>>(src, n->S, use_gelu, n->cpart);
+    else
+        k_center_partials<<<ch * CENTER_PARTS, 256, 0, n->stream>>>(src, n->S, use_gelu, n->cpart);
     k_center_means<<<(ch + 127) / 128, 128, 0, n->stream>>>(n->cpart, ch, n->S, n->hmean);
-    k_center_apply<<<dim3(32, ch), 256, 0, n->stream>>>(src, n->S, use_gelu, n->hmean, n->hs);
+    if (v4)
+        k_center_apply_v<<<dim3(32, ch), 256, 0, n->stream>>>(src, n->S, use_gelu, n->hmean, n->hs);
+    else
+        k_center_apply<<<dim3(32, ch), 256, 0, n->stream>>>(src, n->S, use_gelu, n->hmean, n->hs);
     return cudaGetLastError();
 }
 
 // out[i][j] += sum_{b,s} X[b][i][s] * (Y ? Y[b][j][s] : 1), chunk partials summed in a fixed order
+// Row-vectorised pair sums: the operand with more channels ("big", channel r = blockIdx.y) is
+// read once, 16 bytes at a time; the other's Cs <= RED_SMALL channels (or the plain sum when it is
+// null) accumulate per thread in FP32 (fmaf, positions in order), then across the block in FP64.
+// part[chunk][i Cy + j] as k_reduce_bs.  grid (chunks, big channels); S a multiple of 4.
+constexpr int RED_SMALL = 8;
+
+__global__ void __launch_bounds__(256) k_reduce_pairs(const float* __restrict__ big, const float* __restrict__ small, int Cb,
+                                                      int Cs, int B, long long S, int chunks, int big_is_x, int Cy,
+                                                      float* __restrict__ part) {
+    const int chunk = blockIdx.x, r = blockIdx.y;
+    const long long S4 = S / 4, n4 = (long long)B * S4;
+    const long long per = (n4 + chunks - 1) / chunks;
+    const long long lo = chunk * per, hi = (lo + per < n4) ? lo + per : n4;
+    float acc[RED_SMALL];
+#pragma unroll
+    for (int k = 0; k < RED_SMALL; ++k) acc[k] = 0.0f;
+    for (long long b = lo / S4; b < B && b * S4 < hi; ++b) {
+        const long long g0 = lo > b * S4 ? lo - b * S4 : 0, g1 = hi - b * S4 < S4 ? hi - b * S4 : S4;
+        const float4* xp = reinterpret_cast<const float4*>(big + (b * Cb + r) * S);
+        if (small) {
+            const float4* yp = reinterpret_cast<const float4*>(small + b * Cs * S);
+#pragma unroll 2
+            for (long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+                const float4 x = __ldg(xp + g);
+#pragma unroll
+                for (int k = 0; k < RED_SMALL; ++k)
+                    if (k < Cs) {
+                        const float4 y = __ldg(yp + k * S4 + g);
+                        acc[k] = fmaf(x.x, y.x, acc[k]);
+                        acc[k] = fmaf(x.y, y.y, acc[k]);
+                        acc[k] = fmaf(x.z, y.z, acc[k]);
+                        acc[k] = fmaf(x.w, y.w, acc[k]);
+                    }
+            }
+        } else {
+#pragma unroll 4
+            for (long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+                const float4 x = __ldg(xp + g);
+                acc[0] += x.x;
+                acc[0] += x.y;
+                acc[0] += x.z;
+                acc[0] += x.w;
+            }
+        }
+    }
+    __shared__ double red[8][RED_SMALL];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nk = small ? Cs : 1;
+#pragma unroll
+    for (int k = 0; k < RED_SMALL; ++k)
+        if (k < nk) {
+            double v = acc[k];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
+            if (lane == 0) red[warp][k] = v;
+        }
+    __syncthreads();
+    if ((int)threadIdx.x < nk) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+        const int k = threadIdx.x;
+        const int pairs = small ? Cb * Cs : Cb;
+        const int pair = big_is_x ? r * Cy + k : k * Cy + r;
+        part[(long long)chunk * pairs + pair] = (float)t;
+    }
+}
+
 cudaError_t reduce_bs(lbm_no* n, const float* X, const float* Y, int Cx, int Cy, float* out) {
     const int pairs = Cx * Cy;
+    const bool al = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15u) == 0;
+    if (n->S % 4 == 0 && al && (Y == nullptr || (Cx >= Cy ? Cy : Cx) <= RED_SMALL)) {
+        const bool x_big = Y == nullptr || Cx >= Cy;
+        const float* big = x_big ? X : Y;
+        const float* small = x_big ? Y : X;
+        const int Cb = x_big ? Cx : Cy, Cs = Y == nullptr ? 1 : (x_big ? Cy : Cx);
+        k_reduce_pairs<<<dim3(REDUCE_CHUNKS, Cb), 256, 0, n->stream>>>(big, small, Cb, Cs, n->B, n->S, REDUCE_CHUNKS,
+                                                                        x_big ? 1 : 0, Cy, n->red);
+        k_sum_partials<<<(pairs + 31) / 32, 512, 0, n->stream>>>(n->red, REDUCE_CHUNKS, pairs, out);
+        return cudaGetLastError();
+    }
     k_reduce_bs<<<pairs * REDUCE_CHUNKS, 256, 0, n->stream>>>(X, Y, n->B, Cx, Cy, n->S, REDUCE_CHUNKS, n->red);
-    k_sum_partials<<<(pairs + 255) / 256, 256, 0, n->stream>>>(n->red, REDUCE_CHUNKS, pairs, out);
+    k_sum_partials<<<(pairs + 31) / 32, 512, 0, n->stream>>>(n->red, REDUCE_CHUNKS, pairs, out);
     return cudaGetLastError();
 }
 
@@ -569,6 +1062,11 @@ lbm_status upload_dft(lbm_no* n) {
     return LBM_OK;
 }
 
+// the width-32 mixing kernels apply: W = 32 and the mode matrices 16-byte aligned
+bool mix32(const lbm_no* n, const float* wm) {
+    return n->W == MIX_W && n->B <= MIX_SB && (reinterpret_cast<uintptr_t>(wm) & 15u) == 0;
+}
+
 // spectral convolution of layer l: input h = act(src) (FP32 [B][W][S], act = GELU if use_gelu) ->
 // out (FP32 [B][W][S], overwritten); keeps the mode coefficients in Xh[l] for the weight gradient
 lbm_status spectral_fwd(lbm_no* n, int l, const float* src, int use_gelu, float* out) {
@@ -594,7 +1092,10 @@ lbm_status spectral_fwd(lbm_no* n, int l, const float* src, int use_gelu, float*
     NCK(n, cudaGetLastError(), "dc mode");
     MixDims md{B, W, MX, MY, MZ};
     const unsigned mix_grid = (unsigned)(((long long)MX * MY * MZ + 7) / 8);
-    k_mix_fwd<<<mix_grid, 256, 0, n->stream>>>(n->Xh[l], n->params + n->oWm[l], md, n->yh);
+    if (mix32(n, n->params + n->oWm[l]))
+        k_mix_fwd32<<<mix_grid, 256, 0, n->stream>>>(n->Xh[l], n->params + n->oWm[l], md, n->yh);
+    else
+        k_mix_fwd<<<mix_grid, 256, 0, n->stream>>>(n->Xh[l], n->params + n->oWm[l], md, n->yh);
     NCK(n, cudaGetLastError(), "mix");
     // inverse z: rows (b,o,kx,ky), K = (ri,kz) -> u1 [b][o][kx][ky][ri][z]
     NCK(n, gemm(n, (int)R, 2 * D, 2 * MZ, 1, n->yh, 2 * MZ, 1, 0, n->HZ, 2 * D, 1, 0, n->u1, 2 * D, 1, 0, 1, 0), "iz");
@@ -636,10 +1137,16 @@ lbm_status spectral_bwd(lbm_no* n, int l, const float* dz, float* dh) {
     NCK(n, cudaGetLastError(), "dc mode");
     MixDims md{B, W, MX, MY, MZ};
     const unsigned mix_grid = (unsigned)(((long long)MX * MY * MZ + 7) / 8);
-    k_mix_bwd_w<<<mix_grid, 256, 0, n->stream>>>(n->dyh, n->Xh[l], md,
-                                                                                   n->grads + n->oWm[l]);
-    NCK(n, cudaGetLastError(), "mix dW");
-    k_mix_bwd_x<<<mix_grid, 256, 0, n->stream>>>(n->dyh, n->params + n->oWm[l], md, n->yh);
+    if (mix32(n, n->params + n->oWm[l]) && mix32(n, n->grads + n->oWm[l])) {
+        // the gradient buffer was zeroed by backward() and this is the only writer of the block
+        k_mix_bwd_w32<<<mix_grid, 256, 0, n->stream>>>(n->dyh, n->Xh[l], md, n->grads + n->oWm[l], 0);
+        NCK(n, cudaGetLastError(), "mix dW");
+        k_mix_bwd_x32<<<mix_grid, 256, 0, n->stream>>>(n->dyh, n->params + n->oWm[l], md, n->yh);
+    } else {
+        k_mix_bwd_w<<<mix_grid, 256, 0, n->stream>>>(n->dyh, n->Xh[l], md, n->grads + n->oWm[l]);
+        NCK(n, cudaGetLastError(), "mix dW");
+        k_mix_bwd_x<<<mix_grid, 256, 0, n->stream>>>(n->dyh, n->params + n->oWm[l], md, n->yh);
+    }
     NCK(n, cudaGetLastError(), "mix dX");
     // adjoint of forward z -> t2p layout
     NCK(n, gemm(n, (int)R, 2 * D, 2 * MZ, 1, n->yh, 2 * MZ, 1, 0, n->GZ, 1, 2 * MZ, 0, n->t2p, 2 * D, 1, 0, 1, 0), "fz^T");
@@ -668,8 +1175,14 @@ lbm_status forward(lbm_no* n, int B, const float* in, float* out) {
     const int W = n->W;
     const long long S = n->S, tot = (long long)B * W * S;
     NCK(n, cudaMemcpyAsync(n->a_in, in, sizeof(float) * B * n->Ci * S, cudaMemcpyDefault, n->stream), "input copy");
-    k_lift<<<grid_for(tot), 256, 0, n->stream>>>(n->a_in, n->params + n->oP, n->params + n->op, B, n->Ci, W, S, n->h0,
-                                                n->hb[0]);
+    // the row-vectorised maps need S a multiple of 4; every buffer here is 16-byte aligned
+    const bool rowv = S % 4 == 0;
+    if (rowv && n->Ci <= VEC_CH)
+        k_lift_v<<<grid_rows(S, B), 256, 0, n->stream>>>(n->a_in, n->params + n->oP, n->params + n->op, n->Ci, W, S, n->h0,
+                                                          n->hb[0]);
+    else
+        k_lift<<<grid_for(tot), 256, 0, n->stream>>>(n->a_in, n->params + n->oP, n->params + n->op, B, n->Ci, W, S, n->h0,
+                                                    n->hb[0]);
     NCK(n, cudaGetLastError(), "lift");
     for (int l = 0; l < n->L; ++l) {
         k_f32_to_bf16<<<grid_for((long long)W * W), 256, 0, n->stream>>>(n->params + n->oWc[l], n->wcb + (long long)l * W * W,
@@ -680,12 +1193,20 @@ lbm_status forward(lbm_no* n, int B, const float* in, float* out) {
         NCK(n, gemm(n, (int)S, W, W, B, n->hb[l], 1, S, (long long)W * S, n->wcb + (long long)l * W * W, 1, W, 0, n->z[l], 1,
                     S, (long long)W * S, 0, 1),
             "conv");
-        k_bias_act<<<grid_for(tot), 256, 0, n->stream>>>(n->z[l], n->params + n->obc[l], W, S, tot, l < n->L - 1 ? 1 : 0,
-                                                        n->hb[l + 1]);
+        if (rowv)
+            k_bias_act_v<<<grid_rows(S, (long long)B * W), 256, 0, n->stream>>>(n->z[l], n->params + n->obc[l], W, S,
+                                                                                  l < n->L - 1 ? 1 : 0, n->hb[l + 1]);
+        else
+            k_bias_act<<<grid_for(tot), 256, 0, n->stream>>>(n->z[l], n->params + n->obc[l], W, S, tot,
+                                                            l < n->L - 1 ? 1 : 0, n->hb[l + 1]);
         NCK(n, cudaGetLastError(), "bias act");
     }
-    k_project<<<grid_for((long long)B * n->Co * S), 256, 0, n->stream>>>(n->z[n->L - 1], n->params + n->oQ,
-                                                                        n->params + n->oq, B, W, n->Co, S, out);
+    if (rowv && n->Co <= VEC_CH && (reinterpret_cast<uintptr_t>(out) & 15u) == 0)
+        k_project_v<<<grid_rows(S, B), 256, 0, n->stream>>>(n->z[n->L - 1], n->params + n->oQ, n->params + n->oq, W, n->Co,
+                                                             S, out);
+    else
+        k_project<<<grid_for((long long)B * n->Co * S), 256, 0, n->stream>>>(n->z[n->L - 1], n->params + n->oQ,
+                                                                            n->params + n->oq, B, W, n->Co, S, out);
     NCK(n, cudaGetLastError(), "project");
     return LBM_OK;
 }
@@ -698,7 +1219,10 @@ lbm_status backward(lbm_no* n, const float* dout) {
     // projection
     NCK(n, reduce_bs(n, dout, n->z[L - 1], n->Co, W, n->grads + n->oQ), "projection dW");
     NCK(n, reduce_bs(n, dout, nullptr, n->Co, 1, n->grads + n->oq), "projection db");
-    k_project_bwd_x<<<grid_for(tot), 256, 0, n->stream>>>(dout, n->params + n->oQ, B, W, n->Co, S, n->dh);
+    if (S % 4 == 0 && n->Co <= VEC_CH && (reinterpret_cast<uintptr_t>(dout) & 15u) == 0)
+        k_project_bwd_x_v<<<grid_rows(S, B), 256, 0, n->stream>>>(dout, n->params + n->oQ, W, n->Co, S, n->dh);
+    else
+        k_project_bwd_x<<<grid_for(tot), 256, 0, n->stream>>>(dout, n->params + n->oQ, B, W, n->Co, S, n->dh);
     NCK(n, cudaGetLastError(), "project bwd");
     for (int l = L - 1; l >= 0; --l) {
         k_act_bwd<<<grid_for(tot), 256, 0, n->stream>>>(n->dh, n->z[l], tot, l < L - 1 ? 1 : 0, n->dz, n->dzb);
@@ -721,7 +1245,7 @@ lbm_status backward(lbm_no* n, const float* dout) {
                             part_b + (long long)full * W * W, W, 1, 0, 0, 0),
                     "conv dW rest");
         }
-        k_sum_partials<<<(W * W + 255) / 256, 256, 0, n->stream>>>(n->part, B * nk, W * W, n->grads + n->oWc[l]);
+        k_sum_partials<<<(W * W + 31) / 32, 512, 0, n->stream>>>(n->part, B * nk, W * W, n->grads + n->oWc[l]);
         NCK(n, cudaGetLastError(), "conv dW sum");
         // dh_l = Wc^T dz (conv) + spectral adjoint
         NCK(n, gemm(n, (int)S, W, W, B, n->dzb, 1, S, (long long)W * S, n->wcb + (long long)l * W * W, W, 1, 0, n->dh2, 1, S,
