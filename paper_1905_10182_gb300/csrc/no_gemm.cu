@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/cmlbm.h"
 #include "no_gemm.h"
@@ -381,7 +382,8 @@ constexpr int THREADS = 320;             // warps 0-1 roles, 2-5 and 6-9 the two
 constexpr int ATOM = 64;                 // elements in one swizzled 128-byte row
 constexpr int MAX_STAGES = 16;
 constexpr int SMEM_ALIGN = 1024;         // the 128-byte swizzle repeats every 8 rows = 1024 B
-constexpr int SMEM_USE = 200 * 1024;     // resident B + ring
+constexpr int SMEM_USE = 200 * 1024;     // resident B + ring (+ C staging)
+constexpr int C_STAGE_BYTES = 8 * 2 * 4096;  // two 4 KB boxes per epilogue warp
 // Unused shared memory after the ring: a descriptor whose two strides were read the other way
 // round would still address memory of this block.
 constexpr int SMEM_TAIL = 8192;
@@ -406,6 +408,10 @@ struct Args {
     float alpha;
     int beta;
     int c_vec;
+    // C through shared memory and the copy engine: 0 off (register stores), 1 store, 2 reduce-add
+    // (beta with FP32 C); the map is N-fastest when c_row, else M-fastest; batch as its third dim
+    int c_tma, c_row, c_3d;
+    int c_stage;  // offset of the staging buffers (two 4 KB per epilogue warp) from the resident region
     unsigned int* err;
 };
 
@@ -448,6 +454,41 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, i
 
 // Tile t of the schedule: first batch item b, first row m0, column tile tn (N fastest, then M,
 // then batch items, `pack` items per tile).
+// One 4 KB box of C (32 rows) from shared memory to global memory: plain store or reduce-add.
+__device__ __forceinline__ void tma_store_c(const CUtensorMap* map, uint32_t src, int c0, int c1, int c2, bool three,
+                                            bool reduce) {
+    const uint64_t m = reinterpret_cast<uint64_t>(map);
+    if (reduce) {
+        if (three)
+            asm volatile("cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(m),
+                         "r"(c0), "r"(c1), "r"(c2), "r"(src)
+                         : "memory");
+        else
+            asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(m),
+                         "r"(c0), "r"(c1), "r"(src)
+                         : "memory");
+    } else {
+        if (three)
+            asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(m), "r"(c0),
+                         "r"(c1), "r"(c2), "r"(src)
+                         : "memory");
+        else
+            asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(m), "r"(c0),
+                         "r"(c1), "r"(src)
+                         : "memory");
+    }
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+    const __nv_bfloat162 r = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&r);
+}
+
 __device__ __forceinline__ void tile_coords(const Args& g, long long t, int& b, int& m0, int& tn) {
     const long long per = (long long)g.tiles_m * g.tiles_n;
     const long long bt = t / per;
@@ -533,7 +574,8 @@ __device__ __forceinline__ void store16(const Args& g, long long off0, int n, co
 
 template <int TN>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_gemm_bf16_tma(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, Args g) {
+    k_gemm_bf16_tma(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                    const __grid_constant__ CUtensorMap map_c, Args g) {
     constexpr int B_BLOCK = TN * TK * 2;    // one K block of B: TN rows x 64 K
     constexpr uint32_t TMEM_COLS = 2 * TN;  // two accumulators of 128 lanes x TN FP32 columns
     extern __shared__ uint8_t smem_raw[];
@@ -694,6 +736,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         // ---- epilogue: group e (warps 2-5 or 6-9) takes the tiles of accumulator e; warp w reads
         // accumulator lanes 32 (w mod 4) .. + 31
         const int q = warp & 3, grp = (warp - 2) >> 2;
+        const uint32_t cstage0 = res + (uint32_t)g.c_stage + (uint32_t)(warp - 2) * 8192;
+        uint32_t cstage = cstage0;
         uint32_t lt = 0;
         for (long long t = blockIdx.x; t < g.tiles && !abort_flag; t += gridDim.x, ++lt) {
             const uint32_t a = lt & 1, ause = lt >> 1;
@@ -711,7 +755,71 @@ __global__ void __launch_bounds__(THREADS, 1)
             const bool live = row < g.M && item < g.batch;
             const long long rowoff = (long long)item * g.scb + (long long)row * g.scm;
             const int ncols = min(TN, g.N - n0);
-            for (int c0 = 0; c0 < ncols; c0 += 32) {
+            if (g.c_tma) {
+                // boxes of 32 rows (this warp's lanes) x 32 columns; the copy engine clips rows,
+                // columns and items outside C
+                const int rb = g.pack == 2 ? (q & 1) * 32 : m0 + q * 32, itw = g.pack == 2 ? b + (q >> 1) : b;
+                for (int c0 = 0; c0 < ncols; c0 += 32) {
+                    uint32_t v[2][16];
+                    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * TN + (uint32_t)c0;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j)
+                        if (c0 + 16 * j < ncols) tmem_ld16(taddr + 16 * j, v[j]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    const uint32_t buf = cstage;
+                    cstage = cstage == cstage0 ? cstage0 + 4096 : cstage0;
+                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+                    __syncwarp();
+                    if (g.c_row && !g.out_bf16) {
+                        // 128-byte rows, 128-byte swizzle: 16-byte chunk j of row lane at j ^ (lane mod 8)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const uint32_t* u = &v[j >> 2][4 * (j & 3)];
+                            st_shared_v4(buf + (uint32_t)lane * 128 + ((uint32_t)(j ^ (lane & 7)) << 4),
+                                         __float_as_uint(g.alpha * __uint_as_float(u[0])),
+                                         __float_as_uint(g.alpha * __uint_as_float(u[1])),
+                                         __float_as_uint(g.alpha * __uint_as_float(u[2])),
+                                         __float_as_uint(g.alpha * __uint_as_float(u[3])));
+                        }
+                    } else if (g.c_row) {
+                        // 64-byte rows, 64-byte swizzle: chunk j of row lane at j ^ ((lane / 2) mod 4)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint32_t* u = &v[j >> 1][8 * (j & 1)];
+                            st_shared_v4(buf + (uint32_t)lane * 64 + ((uint32_t)(j ^ ((lane >> 1) & 3)) << 4),
+                                         bf16x2_bits(g.alpha * __uint_as_float(u[0]), g.alpha * __uint_as_float(u[1])),
+                                         bf16x2_bits(g.alpha * __uint_as_float(u[2]), g.alpha * __uint_as_float(u[3])),
+                                         bf16x2_bits(g.alpha * __uint_as_float(u[4]), g.alpha * __uint_as_float(u[5])),
+                                         bf16x2_bits(g.alpha * __uint_as_float(u[6]), g.alpha * __uint_as_float(u[7])));
+                        }
+                    } else if (g.out_bf16) {
+                        // column c at buf + 64 c, row lane at 2 lane
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const __nv_bfloat16 h = __float2bfloat16(g.alpha * __uint_as_float(v[c >> 4][c & 15]));
+                            asm volatile("st.shared.b16 [%0], %1;\n" ::"r"(buf + (uint32_t)(c * 64 + lane * 2)),
+                                         "h"(*reinterpret_cast<const unsigned short*>(&h))
+                                         : "memory");
+                        }
+                    } else {
+                        // column c at buf + 128 c, row lane at 4 lane
+#pragma unroll
+                        for (int c = 0; c < 32; ++c)
+                            asm volatile("st.shared.f32 [%0], %1;\n" ::"r"(buf + (uint32_t)(c * 128 + lane * 4)),
+                                         "f"(g.alpha * __uint_as_float(v[c >> 4][c & 15]))
+                                         : "memory");
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (g.c_row)
+                            tma_store_c(&map_c, buf, n0 + c0, rb, itw, g.c_3d, g.c_tma == 2);
+                        else
+                            tma_store_c(&map_c, buf, rb, n0 + c0, itw, g.c_3d, g.c_tma == 2);
+                    }
+                }
+            }
+            for (int c0 = 0; !g.c_tma && c0 < ncols; c0 += 32) {
                 // two 16-column loads in flight, then one wait
                 uint32_t v[2][16];
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * TN + (uint32_t)c0;
@@ -732,6 +840,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&tempty[a])) : "memory");
         }
+        // the staged boxes have been read and written before the block's shared memory is released
+        if (g.c_tma && lane == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -837,6 +947,49 @@ bool operand_map(CUtensorMap* map, const void* base, int R, int K, int batch, lo
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map of C for the copy-engine epilogue: boxes of 32 rows x 32 columns, N-fastest with the
+// 128-byte (FP32) or 64-byte (BF16) swizzle when C is row-contiguous, M-fastest unswizzled when it
+// is column-contiguous.  False when C does not qualify (alignment, strides, a shared C).
+bool c_map(CUtensorMap* map, const GemmArgs& g, int batch, int* row, int* three) {
+    const EncodeTiled enc = encoder();
+    if (!enc || !aligned16(g.C)) return false;
+    const long long es = g.out_bf16 ? 2 : 4;
+    cuuint64_t dims[3], strides[2];
+    cuuint32_t box[3], estr[3] = {1, 1, 1};
+    CUtensorMapSwizzle sw;
+    if (g.scn == 1 && g.scm > 0 && (g.scm * es) % 16 == 0) {
+        *row = 1;
+        dims[0] = (cuuint64_t)g.N;
+        dims[1] = (cuuint64_t)g.M;
+        strides[0] = (cuuint64_t)(g.scm * es);
+        box[0] = 32;
+        box[1] = 32;
+        sw = g.out_bf16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+    } else if (g.scm == 1 && g.scn > 0 && (g.scn * es) % 16 == 0) {
+        *row = 0;
+        dims[0] = (cuuint64_t)g.M;
+        dims[1] = (cuuint64_t)g.N;
+        strides[0] = (cuuint64_t)(g.scn * es);
+        box[0] = 32;
+        box[1] = 32;
+        sw = CU_TENSOR_MAP_SWIZZLE_NONE;
+    } else {
+        return false;
+    }
+    *three = batch > 1;
+    if (*three) {
+        if (g.scb <= 0 || (g.scb * es) % 16 != 0) return false;
+        dims[2] = (cuuint64_t)batch;
+        strides[1] = (cuuint64_t)(g.scb * es);
+        box[2] = 1;
+    }
+    for (int i = 0; i < 1 + *three; ++i)
+        if (strides[i] >= (1ull << 40)) return false;
+    return enc(map, g.out_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, *three ? 3 : 2, g.C, dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int sm_count() {
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -845,7 +998,7 @@ int sm_count() {
 }
 
 template <int TN>
-cudaError_t launch_tma_tn(const CUtensorMap& ma, const CUtensorMap& mb, tma::Args a, cudaStream_t st) {
+cudaError_t launch_tma_tn(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mc, tma::Args a, cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
         const cudaError_t e =
@@ -855,7 +1008,7 @@ cudaError_t launch_tma_tn(const CUtensorMap& ma, const CUtensorMap& mb, tma::Arg
     }
     static const int sms = sm_count();
     const long long grid = a.tiles < sms ? a.tiles : sms;
-    tma::k_gemm_bf16_tma<TN><<<(unsigned)grid, tma::THREADS, tma::SMEM_BYTES, st>>>(ma, mb, a);
+    tma::k_gemm_bf16_tma<TN><<<(unsigned)grid, tma::THREADS, tma::SMEM_BYTES, st>>>(ma, mb, mc, a);
     return cudaGetLastError();
 }
 
@@ -889,9 +1042,18 @@ bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* 
     a.b_res = !a.b_3d && a.tiles_n == 1 && (long long)a.k_blocks * b_block <= tma::SMEM_USE / 2;
     a.res_bytes = a.b_res ? a.k_blocks * b_block : 0;
     a.stage_bytes = a.a_bytes + (a.b_res ? 0 : b_block);
-    a.stages = (tma::SMEM_USE - a.res_bytes) / a.stage_bytes;
+    // C through the copy engine for the narrower tiles (a 256-column tile keeps its ring deep):
+    // stores, or reduce-adds for beta with FP32 C
+    CUtensorMap mc;
+    memset(&mc, 0, sizeof(mc));
+    a.c_tma = 0;
+    a.c_row = a.c_3d = 0;
+    if (TN <= 128 && (!g.beta || !g.out_bf16) && c_map(&mc, g, batch, &a.c_row, &a.c_3d)) a.c_tma = g.beta ? 2 : 1;
+    const int ring_budget = tma::SMEM_USE - (a.c_tma ? tma::C_STAGE_BYTES : 0);
+    a.stages = (ring_budget - a.res_bytes) / a.stage_bytes;
     if (a.stages > tma::MAX_STAGES) a.stages = tma::MAX_STAGES;
     if (a.stages < 2) return false;
+    a.c_stage = ((a.res_bytes + a.stages * a.stage_bytes) + tma::SMEM_ALIGN - 1) / tma::SMEM_ALIGN * tma::SMEM_ALIGN;
     a.C = g.C;
     a.scm = g.scm;
     a.scn = g.scn;
@@ -902,11 +1064,11 @@ bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* 
     a.c_vec = g.c_vec;
     a.err = g.err;
     if (TN == 64)
-        *err = launch_tma_tn<64>(ma, mb, a, st);
+        *err = launch_tma_tn<64>(ma, mb, mc, a, st);
     else if (TN == 128)
-        *err = launch_tma_tn<128>(ma, mb, a, st);
+        *err = launch_tma_tn<128>(ma, mb, mc, a, st);
     else
-        *err = launch_tma_tn<256>(ma, mb, a, st);
+        *err = launch_tma_tn<256>(ma, mb, mc, a, st);
     return true;
 }
 

@@ -134,12 +134,14 @@ def test_gemm_tma_operand_layouts(a_k, b_k, M, N, K, nb, b_shared):
 
 @pytest.mark.parametrize("out_bf16", [0, 1])
 @pytest.mark.parametrize("c_row_major", [False, True])
-def test_gemm_tma_alpha_beta_epilogue(out_bf16, c_row_major):
-    """The copy-engine path's epilogue: alpha = -0.75 added to the previous C (beta), FP32 or BF16
-    output, C column-major (M contiguous: element by element) or row-major (N contiguous: 16-byte
-    vectors, with a ragged last column chunk)."""
+@pytest.mark.parametrize("beta", [0, 1])
+def test_gemm_tma_alpha_beta_epilogue(out_bf16, c_row_major, beta):
+    """The copy-engine path's epilogue, alpha = -0.75, FP32 or BF16 output, C column-major (M
+    contiguous) or row-major (N contiguous), ragged rows and a ragged last column box: stored
+    through shared memory by the copy engine (beta = 0), added to the previous C by its reduce-add
+    (beta, FP32), or stored from registers after loading the previous C (beta, BF16)."""
     M, N, K, nb = 260, 72, 96, 2
-    rng = np.random.default_rng(77 + out_bf16 + 2 * c_row_major)
+    rng = np.random.default_rng(77 + out_bf16 + 2 * c_row_major + 4 * beta)
     a, Ad, sa = _operand(rng, M, K, nb, True, 0)
     b, Bd, sbt = _operand(rng, N, K, nb, False, 8)
     sb = (sbt[1], sbt[0], sbt[2])
@@ -152,10 +154,10 @@ def test_gemm_tma_alpha_beta_epilogue(out_bf16, c_row_major):
         sc = (1, M, N * M)
     C = torch.from_numpy(c0).to(dt).cuda()
     c0 = C.float().cpu().numpy().astype(np.float64)
-    _gemm(M, N, K, nb, Ad, sa, Bd, sb, C, sc, out_bf16=out_bf16, alpha=-0.75, beta=1)
+    _gemm(M, N, K, nb, Ad, sa, Bd, sb, C, sc, out_bf16=out_bf16, alpha=-0.75, beta=beta)
     eq = "imk,ink->imn" if c_row_major else "imk,ink->inm"
     prod = np.einsum(eq, a, b)
-    ref = c0 - 0.75 * prod
+    ref = beta * c0 - 0.75 * prod
     bound = 0.75 * 2.0 ** -20 * np.einsum(eq, np.abs(a), np.abs(b))
     if out_bf16:
         bound = bound + 2.0 ** -8 * np.abs(ref)
