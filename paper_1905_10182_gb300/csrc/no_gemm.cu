@@ -21,6 +21,7 @@
 #include <cuda.h>  // CUtensorMap and the tensor-map encoder (resolved through the runtime at first use)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <stdint.h>
 #include <string.h>
 
@@ -397,7 +398,11 @@ struct Args {
     int a_mn, b_mn;   // operand M- (N-) contiguous rather than K-contiguous
     int a_3d, b_3d;   // tensor map carries the batch as its third dimension
     int a_kbox;       // K depth of an M-major A box (64, or K rounded up to 16 when K < 64)
-    int a_bytes;      // bytes of one A block (128 rows x 64 K, or 2 atoms x a_kbox K rows)
+    int a_bytes;      // shared memory of one A block in a stage (128 rows x 64 K, or 2 atoms x a_kbox K rows)
+    int stage_tx;     // bytes the copies of one stage deliver (boxes no taller than the operand)
+    int b_tx;         // ... of which B's (per K block, also for the resident B)
+    int ksplit, kchunk_blocks;  // K slices per item and K blocks per slice
+    int l2_prefetch;            // the producer also prefetches into L2 one ring length ahead
     int b_res;        // B loaded once (every K block of the single column tile) and kept
     int stages;       // ring stages
     int stage_bytes;  // A block (+ B block unless resident)
@@ -452,8 +457,8 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, i
             : "memory");
 }
 
-// Tile t of the schedule: first batch item b, first row m0, column tile tn (N fastest, then M,
-// then batch items, `pack` items per tile).
+// Tile t of the schedule: first batch item b, K slice ks, first row m0, column tile tn (N fastest,
+// then M, then K slices, then batch items, `pack` items per tile).
 // One 4 KB box of C (32 rows) from shared memory to global memory: plain store or reduce-add.
 __device__ __forceinline__ void tma_store_c(const CUtensorMap* map, uint32_t src, int c0, int c1, int c2, bool three,
                                             bool reduce) {
@@ -489,13 +494,31 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
     return *reinterpret_cast<const uint32_t*>(&r);
 }
 
-__device__ __forceinline__ void tile_coords(const Args& g, long long t, int& b, int& m0, int& tn) {
+// Prefetch of the box at (c0, c1[, c2]) into L2 (no shared-memory destination, no completion).
+__device__ __forceinline__ void tma_prefetch(const CUtensorMap* map, int c0, int c1, int c2, bool three) {
+    const uint64_t m = reinterpret_cast<uint64_t>(map);
+    if (three)
+        asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];\n" ::"l"(m), "r"(c0), "r"(c1), "r"(c2)
+                     : "memory");
+    else
+        asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];\n" ::"l"(m), "r"(c0), "r"(c1) : "memory");
+}
+
+__device__ __forceinline__ void tile_coords(const Args& g, long long t, int& b, int& m0, int& tn, int& ks) {
     const long long per = (long long)g.tiles_m * g.tiles_n;
-    const long long bt = t / per;
-    const int r = (int)(t - bt * per);
+    const long long bk = t / per;
+    const int r = (int)(t - bk * per);
+    const long long bt = bk / g.ksplit;
+    ks = (int)(bk - bt * g.ksplit);
     b = (int)bt * g.pack;
     m0 = (r / g.tiles_n) * TM;
     tn = r % g.tiles_n;
+}
+
+// K blocks of a tile of K slice ks (the last slice may be shorter)
+__device__ __forceinline__ int tile_kblocks(const Args& g, int ks) {
+    const int rest = g.k_blocks - ks * g.kchunk_blocks;
+    return rest < g.kchunk_blocks ? rest : g.kchunk_blocks;
 }
 
 // One accumulator chunk of 16 FP32 columns (tcgen05.ld 32 lanes x 32 bit, 16 repetitions); the
@@ -621,7 +644,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             // the whole (shared) B once: K block kb at res + kb * B_BLOCK
             const uint32_t bar = smem_u32(&bres);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
-                         "r"((uint32_t)(g.k_blocks * B_BLOCK))
+                         "r"((uint32_t)(g.k_blocks * g.b_tx))
                          : "memory");
             for (int kb = 0; kb < g.k_blocks; ++kb) {
                 const uint32_t sb = res + (uint32_t)(kb * B_BLOCK);
@@ -634,20 +657,56 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
         }
         uint32_t it = 0, s = 0, ph = 0;  // blocks issued; stage and the parity of its current use
+        // L2 prefetch cursor, one ring length ahead of the loads: the copy engine keeps few
+        // DRAM-bound requests in flight per SM, so the loads should find their data in L2
+        long long pt = blockIdx.x;
+        int pb = 0, pm0 = 0, ptn = 0, pks = 0, pkb = 0, pnkb = 0;
+        if (pt < g.tiles) {
+            tile_coords(g, pt, pb, pm0, ptn, pks);
+            pnkb = tile_kblocks(g, pks);
+        }
+        auto prefetch_next = [&]() {
+            if (pt >= g.tiles) return;
+            const int k0 = (pks * g.kchunk_blocks + pkb) * TK;
+            if (g.a_mn) {
+                tma_prefetch(&map_a, pm0, k0, pb, g.a_3d);
+                if (g.pack == 1) tma_prefetch(&map_a, pm0 + ATOM, k0, pb, g.a_3d);
+            } else {
+                tma_prefetch(&map_a, k0, pm0, pb, g.a_3d);
+            }
+            if (!g.b_res) {
+                if (g.b_mn) {
+                    for (int j = 0; j < TN / ATOM; ++j) tma_prefetch(&map_b, ptn * TN + j * ATOM, k0, pb, g.b_3d);
+                } else {
+                    tma_prefetch(&map_b, k0, ptn * TN, pb, g.b_3d);
+                }
+            }
+            if (++pkb == pnkb) {
+                pkb = 0;
+                pt += gridDim.x;
+                if (pt < g.tiles) {
+                    tile_coords(g, pt, pb, pm0, ptn, pks);
+                    pnkb = tile_kblocks(g, pks);
+                }
+            }
+        };
+        if (g.l2_prefetch)
+            for (uint32_t j = 0; j < stages; ++j) prefetch_next();
         for (long long t = blockIdx.x; t < g.tiles && !abort_flag; t += gridDim.x) {
-            int b, m0, tn;
-            tile_coords(g, t, b, m0, tn);
-            const int n0 = tn * TN;
-            for (int kb = 0; kb < g.k_blocks; ++kb, ++it, s = (s + 1 == stages) ? (ph ^= 1u, 0u) : s + 1) {
+            int b, m0, tn, ks;
+            tile_coords(g, t, b, m0, tn, ks);
+            const int n0 = tn * TN, nkb = tile_kblocks(g, ks);
+            for (int kb = 0; kb < nkb; ++kb, ++it, s = (s + 1 == stages) ? (ph ^= 1u, 0u) : s + 1) {
                 if (!wait_or_abort(smem_u32(&empty[s]), ph ^ 1, &abort_flag)) {
                     abort_flag = 1;
                     break;
                 }
+                if (g.l2_prefetch) prefetch_next();
                 const uint32_t bar = smem_u32(&full[s]);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(stage_bytes)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(g.stage_tx)
                              : "memory");
                 const uint32_t sa = ring + s * stage_bytes, sb = sa + (uint32_t)g.a_bytes;
-                const int k0 = kb * TK;
+                const int k0 = (ks * g.kchunk_blocks + kb) * TK;
                 if (g.a_mn) {
                     // two 64-row atoms: rows m0 .. m0 + 127 of one item, or (packed) rows 0 .. 63 of
                     // items b and b + 1 in one box
@@ -690,7 +749,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint32_t d = tmem + a * TN;
-            for (int kb = 0; kb < g.k_blocks; ++kb, s = (s + 1 == stages) ? (ph ^= 1u, 0u) : s + 1) {
+            int tb, tm0, ttn, ks;
+            tile_coords(g, t, tb, tm0, ttn, ks);
+            const int nkb = tile_kblocks(g, ks), kb0 = ks * g.kchunk_blocks;
+            for (int kb = 0; kb < nkb; ++kb, s = (s + 1 == stages) ? (ph ^= 1u, 0u) : s + 1) {
                 if (!wait_or_abort(smem_u32(&full[s]), ph, &abort_flag)) {
                     ok = false;
                     break;
@@ -698,7 +760,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t sa = ring + s * stage_bytes;
                 const uint32_t sb = g.b_res ? res + (uint32_t)(kb * B_BLOCK) : sa + (uint32_t)g.a_bytes;
-                const int kmax = min(TK, ((g.K - kb * TK + 15) >> 4) << 4);
+                const int kmax = min(TK, ((g.K - (kb0 + kb) * TK + 15) >> 4) << 4);
 #pragma unroll
                 for (int j = 0; j < TK / 16; ++j) {
                     if (16 * j >= kmax) break;  // zero padding past the end of K: no MMA
@@ -742,8 +804,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (long long t = blockIdx.x; t < g.tiles && !abort_flag; t += gridDim.x, ++lt) {
             const uint32_t a = lt & 1, ause = lt >> 1;
             if ((int)a != grp) continue;
-            int b, m0, tn;
-            tile_coords(g, t, b, m0, tn);
+            int b, m0, tn, ks;
+            tile_coords(g, t, b, m0, tn, ks);
             const int n0 = tn * TN;
             if (!wait_or_abort(smem_u32(&tfull[a]), ause & 1, &abort_flag)) {
                 abort_flag = 1;
@@ -753,12 +815,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int r = q * 32 + lane;  // row of the tile
             const int item = g.pack == 2 ? b + (r >> 6) : b, row = g.pack == 2 ? (r & 63) : m0 + r;
             const bool live = row < g.M && item < g.batch;
-            const long long rowoff = (long long)item * g.scb + (long long)row * g.scm;
+            const long long rowoff = ((long long)item * g.ksplit + ks) * g.scb + (long long)row * g.scm;
             const int ncols = min(TN, g.N - n0);
             if (g.c_tma) {
                 // boxes of 32 rows (this warp's lanes) x 32 columns; the copy engine clips rows,
                 // columns and items outside C
-                const int rb = g.pack == 2 ? (q & 1) * 32 : m0 + q * 32, itw = g.pack == 2 ? b + (q >> 1) : b;
+                const int rb = g.pack == 2 ? (q & 1) * 32 : m0 + q * 32;
+                const int itw = (g.pack == 2 ? b + (q >> 1) : b) * g.ksplit + ks;
                 for (int c0 = 0; c0 < ncols; c0 += 32) {
                     uint32_t v[2][16];
                     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * TN + (uint32_t)c0;
@@ -1015,18 +1078,25 @@ cudaError_t launch_tma_tn(const CUtensorMap& ma, const CUtensorMap& mb, const CU
 // The TMA kernel when both operands allow it (and K > 0); false: use the register-staged kernel.
 bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* err) {
     if (g.K <= 0) return false;
+    const int ksplit = g.ksplit > 1 ? g.ksplit : 1;
+    if (ksplit > 1 && (g.kchunk <= 0 || g.kchunk % TK != 0 || (long long)(ksplit - 1) * g.kchunk >= g.K ||
+                       (long long)ksplit * g.kchunk < g.K))
+        return false;
     const int TN = g.N <= 64 ? 64 : (g.N <= 128 ? 128 : 256);
     CUtensorMap ma, mb;
     tma::Args a;
     // items of at most 64 rows against one shared B: two per 128-row tile
-    a.pack = (g.M <= tma::ATOM && batch > 1 && g.sbb == 0 && g.sab != 0) ? 2 : 1;
-    // an M-major A box only as deep in K as a short K needs (rounded up to the MMA depth)
+    a.pack = (ksplit == 1 && g.M <= tma::ATOM && batch > 1 && g.sbb == 0 && g.sab != 0) ? 2 : 1;
+    // an M-major A box only as deep in K as a short K needs (rounded up to the MMA depth); a
+    // K-major box only as tall as the operand (rows past it in the stage are never stored)
     const int kbox = g.K < TK ? ((g.K + 15) >> 4) << 4 : TK;
+    const int a_rows = a.pack == 2 ? tma::ATOM : std::min(TM, (g.M + 7) / 8 * 8);
+    const int b_rows = std::min(TN, (g.N + 7) / 8 * 8);
     const bool a_mn_layout = !(g.sak == 1 && g.sam > 0 && g.sam % 8 == 0);
-    if (!operand_map(&ma, g.A, g.M, g.K, batch, g.sam, g.sak, g.sab, TM / a.pack, a.pack, a_mn_layout ? kbox : TK,
-                     &a.a_mn, &a.a_3d))
+    if (!operand_map(&ma, g.A, g.M, g.K, batch, g.sam, g.sak, g.sab, a_rows, a.pack, a_mn_layout ? kbox : TK, &a.a_mn,
+                     &a.a_3d))
         return false;
-    if (!operand_map(&mb, g.B, g.N, g.K, batch, g.sbn, g.sbk, g.sbb, TN, 1, TK, &a.b_mn, &a.b_3d)) return false;
+    if (!operand_map(&mb, g.B, g.N, g.K, batch, g.sbn, g.sbk, g.sbb, b_rows, 1, TK, &a.b_mn, &a.b_3d)) return false;
     a.M = g.M;
     a.N = g.N;
     a.K = g.K;
@@ -1034,26 +1104,41 @@ bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* 
     a.tiles_m = (g.M + TM - 1) / TM;
     a.tiles_n = (g.N + TN - 1) / TN;
     a.k_blocks = (g.K + TK - 1) / TK;
-    a.tiles = (long long)a.tiles_m * a.tiles_n * ((batch + a.pack - 1) / a.pack);
+    a.ksplit = ksplit;
+    a.kchunk_blocks = ksplit > 1 ? g.kchunk / TK : a.k_blocks;
+    a.tiles = (long long)a.tiles_m * a.tiles_n * ((batch + a.pack - 1) / a.pack) * ksplit;
     a.a_kbox = a.a_mn ? kbox : TK;
-    a.a_bytes = a.a_mn ? 2 * tma::ATOM * a.a_kbox * 2 : TM * TK * 2;
+    // a stage holds exactly the boxes (multiples of 1024 B, so every region keeps the swizzle
+    // alignment); the MMAs still read 128 rows of A and TN rows of B, and rows past a short box
+    // (garbage in the accumulator rows / columns that are never stored) may lie in the next stage
+    const int a_tx = a.a_mn ? 2 * tma::ATOM * a.a_kbox * 2 : a_rows * a.pack * TK * 2;
+    a.b_tx = a.b_mn ? TN * TK * 2 : b_rows * TK * 2;
+    a.a_bytes = a_tx;
     const int b_block = TN * TK * 2;
-    // one B for every tile (shared by the batch, one column tile) that fits in half the budget
-    a.b_res = !a.b_3d && a.tiles_n == 1 && (long long)a.k_blocks * b_block <= tma::SMEM_USE / 2;
+    // one B for every tile (shared by the batch, one column tile, no K slices) that fits in half
+    // the budget
+    a.b_res = ksplit == 1 && !a.b_3d && a.tiles_n == 1 && (long long)a.k_blocks * b_block <= tma::SMEM_USE / 2;
     a.res_bytes = a.b_res ? a.k_blocks * b_block : 0;
-    a.stage_bytes = a.a_bytes + (a.b_res ? 0 : b_block);
+    a.stage_bytes = a_tx + (a.b_res ? 0 : a.b_tx);
+    a.stage_tx = a.stage_bytes;
+    a.l2_prefetch = 1;
+    // what the last stage's MMAs read past the end of the ring: kept inside the block's memory
+    int guard = std::max(0, (a.a_mn ? a_tx : TM * TK * 2) - a.stage_bytes);
+    if (!a.b_res) guard = std::max(guard, a_tx + b_block - a.stage_bytes);
+    guard = (guard + tma::SMEM_ALIGN - 1) / tma::SMEM_ALIGN * tma::SMEM_ALIGN;
     // C through the copy engine for the narrower tiles (a 256-column tile keeps its ring deep):
     // stores, or reduce-adds for beta with FP32 C
     CUtensorMap mc;
     memset(&mc, 0, sizeof(mc));
     a.c_tma = 0;
     a.c_row = a.c_3d = 0;
-    if (TN <= 128 && (!g.beta || !g.out_bf16) && c_map(&mc, g, batch, &a.c_row, &a.c_3d)) a.c_tma = g.beta ? 2 : 1;
-    const int ring_budget = tma::SMEM_USE - (a.c_tma ? tma::C_STAGE_BYTES : 0);
+    if (TN <= 128 && (!g.beta || !g.out_bf16) && c_map(&mc, g, batch * ksplit, &a.c_row, &a.c_3d))
+        a.c_tma = g.beta ? 2 : 1;
+    const int ring_budget = tma::SMEM_USE - (a.c_tma ? tma::C_STAGE_BYTES : 0) - guard;
     a.stages = (ring_budget - a.res_bytes) / a.stage_bytes;
     if (a.stages > tma::MAX_STAGES) a.stages = tma::MAX_STAGES;
     if (a.stages < 2) return false;
-    a.c_stage = ((a.res_bytes + a.stages * a.stage_bytes) + tma::SMEM_ALIGN - 1) / tma::SMEM_ALIGN * tma::SMEM_ALIGN;
+    a.c_stage = ((a.res_bytes + a.stages * a.stage_bytes + guard) + tma::SMEM_ALIGN - 1) / tma::SMEM_ALIGN * tma::SMEM_ALIGN;
     a.C = g.C;
     a.scm = g.scm;
     a.scn = g.scn;
@@ -1082,6 +1167,7 @@ cudaError_t launch_gemm_bf16(const GemmArgs& g_in, int batch, cudaStream_t st) {
     g.c_vec = (g.scn == 1 && g.scm % per == 0 && (batch == 1 || g.scb % per == 0) && aligned16(g.C)) ? (g.out_bf16 ? 2 : 1) : 0;
     cudaError_t e = cudaSuccess;
     if (try_launch_tma(g, batch, st, &e)) return e;
+    if (g.ksplit > 1) return cudaErrorNotSupported;  // split-K needs the copy-engine path
     g.a_mode = stage_mode(g.A, g.sam, g.sak, g.sab, batch);
     g.b_mode = stage_mode(g.B, g.sbn, g.sbk, g.sbb, batch);
     if (g.N <= 32) return launch_tn<32>(g, batch, st);

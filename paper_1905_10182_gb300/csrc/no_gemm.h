@@ -28,6 +28,11 @@ struct GemmArgs {
     // register-staged kernel (0 element by element, 1 K-contiguous 16-byte rows, 2 row-contiguous
     // 8 x 8 blocks); C stored as 16-byte vectors (1 FP32, 2 BF16) or element by element (0)
     int a_mode, b_mode, c_vec;
+    // split-K into partial products (copy-engine path only): item b's K range is cut into ksplit
+    // slices of kchunk elements (a multiple of 64; the last slice shorter), slice j of item b
+    // written to C item b * ksplit + j.  ksplit = 1: the plain product.
+    int ksplit = 1;
+    int kchunk = 0;
 };
 
 cudaError_t launch_gemm_bf16(const GemmArgs& g, int batch, cudaStream_t st);

@@ -177,12 +177,44 @@ __global__ void __launch_bounds__(256) k_center_partials_v(const float* __restri
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-__global__ void k_center_means(const double* __restrict__ part, int channels, long long S, float* __restrict__ mean) {
-    const int bc = blockIdx.x * blockDim.x + threadIdx.x;
+// one warp per channel: mean[bc] = (sum of its parts) / S, the parts split over the lanes and the
+// lanes' sums combined by a shuffle tree (FP64)
+__global__ void k_center_means(const double* __restrict__ part, int channels, int parts, long long S, float* __restrict__ mean) {
+    const int bc = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (bc >= channels) return;
     double t = 0.0;
-    for (int p = 0; p < CENTER_PARTS; ++p) t += part[bc * CENTER_PARTS + p];
-    mean[bc] = (float)(t / (double)S);
+    for (int p = lane; p < parts; p += 32) t += part[(long long)bc * parts + p];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xFFFFFFFFu, t, off);
+    if (lane == 0) mean[bc] = (float)(t / (double)S);
+}
+
+// db[o] += sum over samples and parts of the per-row partial sums part[(b W + o) parts + p]; one
+// warp per o
+__global__ void k_rows_to_bias(const double* __restrict__ part, int B, int W, int parts, float* __restrict__ db) {
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (o >= W) return;
+    double t = 0.0;
+    for (int b = 0; b < B; ++b)
+        for (int p = lane; p < parts; p += 32) t += part[((long long)b * W + o) * parts + p];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xFFFFFFFFu, t, off);
+    if (lane == 0) db[o] += (float)t;
+}
+
+// Sum of one FP32 value per thread over a block of 256 threads in FP64, written by thread 0.
+__device__ __forceinline__ void block_sum_to(float v, double* out) {
+    __shared__ double red[8];
+    double d = v;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xFFFFFFFFu, d, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        *out = t;
+    }
 }
 
 // grid (chunks, channels): each block strides over its channel's S values
@@ -645,6 +677,30 @@ __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t
     if (threadIdx.x == 0) atomicAdd(loss, sh[0] / (double)n);
 }
 
+__device__ __forceinline__ void adam1(float& p, float g, float& m, float& v, float lr, float b1, float b2, float eps, float c1,
+                                      float c2) {
+    m = b1 * m + (1.0f - b1) * g;
+    v = b2 * v + (1.0f - b2) * g * g;
+    p -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
+// The same update four parameters per access (n4 = n / 4 float4 groups; the tail goes to k_adam).
+__global__ void __launch_bounds__(256) k_adam_v(float4* __restrict__ p, const float4* __restrict__ g, float4* __restrict__ m,
+                                                float4* __restrict__ v, long long n4, float lr, float b1, float b2, float eps,
+                                                float c1, float c2) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+        const float4 gi = g[i];
+        float4 pi = p[i], mi = m[i], vi = v[i];
+        adam1(pi.x, gi.x, mi.x, vi.x, lr, b1, b2, eps, c1, c2);
+        adam1(pi.y, gi.y, mi.y, vi.y, lr, b1, b2, eps, c1, c2);
+        adam1(pi.z, gi.z, mi.z, vi.z, lr, b1, b2, eps, c1, c2);
+        adam1(pi.w, gi.w, mi.w, vi.w, lr, b1, b2, eps, c1, c2);
+        p[i] = pi;
+        m[i] = mi;
+        v[i] = vi;
+    }
+}
+
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v, long long n,
                        float lr, float b1, float b2, float eps, float c1, float c2) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -667,26 +723,64 @@ inline unsigned grid_for(long long n, int threads = 256) {
 // ---- row-vectorised forms of the pointwise maps (S a multiple of 4, buffers 16-byte aligned):
 // a thread takes four consecutive positions of one sample; channel loops run over registers.
 constexpr int VEC_CH = 8;  // input channels of the lift / output channels of the projection held in registers
+constexpr int ROW_PER = 8;  // float4 groups per thread in the row kernels that also sum their row
 
 inline dim3 grid_rows(long long S, long long rows) { return dim3((unsigned)((S / 4 + 255) / 256), (unsigned)rows); }
+// blocks of 256 threads x ROW_PER float4 groups per row
+inline int row_blocks(long long S) { return (int)((S / 4 + 256 * ROW_PER - 1) / (256 * ROW_PER)); }
 
 
-// z[b][o][s] += bias[o]; hb = act(z) (BF16); grid (positions / 1024, B W)
+// z[b][o][s] += bias[o]; hb = act(z) (BF16); grid (row_blocks(S), B W), ROW_PER float4 groups per
+// thread.  part (optional): the block's FP64 sum of act(z) at part[row gridDim.x + blockIdx.x],
+// the next layer's centring sums.
 __global__ void __launch_bounds__(256) k_bias_act_v(float* __restrict__ z, const float* __restrict__ bias, int W, long long S,
-                                                    int use_gelu, bf16* __restrict__ hb) {
-    const long long s4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s4 * 4 >= S) return;
-    const long long row = blockIdx.y;
+                                                    int use_gelu, bf16* __restrict__ hb, double* __restrict__ part) {
+    const long long row = blockIdx.y, S4 = S / 4;
     const float bo = bias[row % W];
-    float4* zp = reinterpret_cast<float4*>(z + row * S) + s4;
-    float4 v = *zp;
-    v.x += bo;
-    v.y += bo;
-    v.z += bo;
-    v.w += bo;
-    *zp = v;
-    if (use_gelu) v = make_float4(gelu(v.x), gelu(v.y), gelu(v.z), gelu(v.w));
-    reinterpret_cast<uint2*>(hb + row * S)[s4] = pack_bf16x4(v);
+    float4* zr = reinterpret_cast<float4*>(z + row * S);
+    uint2* hr = reinterpret_cast<uint2*>(hb + row * S);
+    float sum = 0.0f;
+#pragma unroll
+    for (int j = 0; j < ROW_PER; ++j) {
+        const long long s4 = ((long long)blockIdx.x * ROW_PER + j) * blockDim.x + threadIdx.x;
+        if (s4 < S4) {
+            float4 v = zr[s4];
+            v.x += bo;
+            v.y += bo;
+            v.z += bo;
+            v.w += bo;
+            zr[s4] = v;
+            if (use_gelu) v = make_float4(gelu(v.x), gelu(v.y), gelu(v.z), gelu(v.w));
+            hr[s4] = pack_bf16x4(v);
+            sum += v.x + v.y + v.z + v.w;
+        }
+    }
+    if (part) block_sum_to(sum, part + row * gridDim.x + blockIdx.x);
+}
+
+// dz = dh act'(z) (FP32 and BF16), row-vectorised; grid (row_blocks(S), B W).  part: the block's
+// FP64 sum of dz at part[row gridDim.x + blockIdx.x] (centring and bias gradient).
+__global__ void __launch_bounds__(256) k_act_bwd_v(const float* __restrict__ dh, const float* __restrict__ z, long long S,
+                                                   int use_gelu, float* __restrict__ dz, bf16* __restrict__ dzb,
+                                                   double* __restrict__ part) {
+    const long long row = blockIdx.y, S4 = S / 4;
+    float sum = 0.0f;
+#pragma unroll
+    for (int j = 0; j < ROW_PER; ++j) {
+        const long long s4 = ((long long)blockIdx.x * ROW_PER + j) * blockDim.x + threadIdx.x;
+        if (s4 < S4) {
+            const long long i = row * S4 + s4;
+            float4 v = __ldg(reinterpret_cast<const float4*>(dh) + i);
+            if (use_gelu) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(z) + i);
+                v = make_float4(v.x * gelu_grad(x.x), v.y * gelu_grad(x.y), v.z * gelu_grad(x.z), v.w * gelu_grad(x.w));
+            }
+            reinterpret_cast<float4*>(dz)[i] = v;
+            reinterpret_cast<uint2*>(dzb)[i] = pack_bf16x4(v);
+            sum += v.x + v.y + v.z + v.w;
+        }
+    }
+    if (part) block_sum_to(sum, part + row * gridDim.x + blockIdx.x);
 }
 
 // h[b][c][s] = p[c] + sum_i P[c][i] a[b][i][s] (Ci <= VEC_CH), h also as BF16; grid (positions / 1024, B)
@@ -808,7 +902,8 @@ struct lbm_no {
     float* dyh = nullptr;
     bf16* hs = nullptr;       // centred BF16 input of the spectral transforms [B][W][S]
     float* hmean = nullptr;   // its per-(sample, channel) means [B][W]
-    double* cpart = nullptr;  // partial sums of the centring [B][W][CENTER_PARTS]
+    double* cpart = nullptr;  // partial sums of the centring [B][W][parts], parts <= max(CENTER_PARTS, rowparts)
+    int rowparts = 0;         // blocks per row of the row-vectorised kernels (0: S not a multiple of 4)
     float* red = nullptr;     // per-chunk partials of the gradient reductions [REDUCE_CHUNKS][pairs]
     float *dh = nullptr, *dh2 = nullptr, *dz = nullptr;
     bf16* dzb = nullptr;
@@ -838,7 +933,7 @@ constexpr int KSPLIT = 1024;  // K chunk of the split-K 1x1 weight gradient (256
 
 cudaError_t gemm(lbm_no* n, int M, int N, int K, int batch, const bf16* A, long long sam, long long sak, long long sab,
                  const bf16* Bm, long long sbk, long long sbn, long long sbb, void* C, long long scm, long long scn,
-                 long long scb, int out_bf16, int beta) {
+                 long long scb, int out_bf16, int beta, int ksplit = 1, int kchunk = 0) {
     GemmArgs g;
     g.M = M;
     g.N = N;
@@ -858,6 +953,8 @@ cudaError_t gemm(lbm_no* n, int M, int N, int K, int batch, const bf16* A, long 
     g.out_bf16 = out_bf16;
     g.alpha = 1.0f;
     g.beta = beta;
+    g.ksplit = ksplit;
+    g.kchunk = kchunk;
     g.err = n->gemm_err;
     return launch_gemm_bf16(g, batch, n->stream);
 }
@@ -894,14 +991,19 @@ cudaError_t permute(lbm_no* n, const bf16* in, bf16* out, const long long din[6]
 constexpr int REDUCE_CHUNKS = 64;  // chunks of the B * S positions in a gradient reduction
 
 // hs = bf16(act(src) - mean), hmean = the per-(sample, channel) means (see k_center_partials)
-cudaError_t center(lbm_no* n, const float* src, int use_gelu) {
+// parts > 0: the row sums of act(src) are already in cpart, `parts` per row (written by the kernel
+// that produced src)
+cudaError_t center(lbm_no* n, const float* src, int use_gelu, int parts = 0) {
     const int ch = n->B * n->W;
     const bool v4 = n->S % 4 == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
-    if (v4)
-        k_center_partials_v<<<ch * CENTER_PARTS, 256, 0, n->stream>>>(src, n->S, use_gelu, n->cpart);
-    else
-        k_center_partials<<<ch * CENTER_PARTS, 256, 0, n->stream>>>(src, n->S, use_gelu, n->cpart);
-    k_center_means<<<(ch + 127) / 128, 128, 0, n->stream>>>(n->cpart, ch, n->S, n->hmean);
+    if (parts <= 0) {
+        parts = CENTER_PARTS;
+        if (v4)
+            k_center_partials_v<<<ch * CENTER_PARTS, 256, 0, n->stream>>>(src, n->S, use_gelu, n->cpart);
+        else
+            k_center_partials<<<ch * CENTER_PARTS, 256, 0, n->stream>>>(src, n->S, use_gelu, n->cpart);
+    }
+    k_center_means<<<(ch + 3) / 4, 128, 0, n->stream>>>(n->cpart, ch, parts, n->S, n->hmean);
     if (v4)
         k_center_apply_v<<<dim3(32, ch), 256, 0, n->stream>>>(src, n->S, use_gelu, n->hmean, n->hs);
     else
@@ -1069,11 +1171,12 @@ bool mix32(const lbm_no* n, const float* wm) {
 
 // spectral convolution of layer l: input h = act(src) (FP32 [B][W][S], act = GELU if use_gelu) ->
 // out (FP32 [B][W][S], overwritten); keeps the mode coefficients in Xh[l] for the weight gradient
-lbm_status spectral_fwd(lbm_no* n, int l, const float* src, int use_gelu, float* out) {
+// parts > 0: the centring sums of act(src) are already in cpart (see center)
+lbm_status spectral_fwd(lbm_no* n, int l, const float* src, int use_gelu, float* out, int parts) {
     const int B = n->B, W = n->W, D = n->D, MX = n->MX, MY = n->MY, MZ = n->MZ;
     const long long D2 = (long long)D * D;
     const long long BWD = (long long)B * W * D;
-    NCK(n, center(n, src, use_gelu), "centre");
+    NCK(n, center(n, src, use_gelu, parts), "centre");
     // x: [bcz][y][x] x FX -> t1 [bcz][(kx,ri)][y]
     NCK(n, gemm(n, D, 2 * MX, D, (int)BWD, n->hs, D, 1, D2, n->FX, 2 * MX, 1, 0, n->t1, 1, D, 2LL * MX * D, 1, 0), "fx");
     // y: rows (bcz,kx), K = (ri,y) -> t2 [b][c][z][kx][ri][ky]
@@ -1113,13 +1216,13 @@ lbm_status spectral_fwd(lbm_no* n, int l, const float* src, int use_gelu, float*
 
 // adjoint of the spectral convolution of layer l: dzb (BF16 gradient of its output) -> dh
 // (FP32, accumulated); adds the mixing-weight gradient
-lbm_status spectral_bwd(lbm_no* n, int l, const float* dz, float* dh) {
+lbm_status spectral_bwd(lbm_no* n, int l, const float* dz, float* dh, int parts) {
     const int B = n->B, W = n->W, D = n->D, MX = n->MX, MY = n->MY, MZ = n->MZ;
     const long long D2 = (long long)D * D;
     const long long BWD = (long long)B * W * D;
     const long long R = (long long)B * W * MX * MY;
     // the adjoint transforms take the centred gradient too (see k_center_partials)
-    NCK(n, center(n, dz, 0), "centre");
+    NCK(n, center(n, dz, 0, parts), "centre");
     // adjoint of inverse x -> u2 layout
     NCK(n, gemm(n, D, 2 * MX, D, (int)BWD, n->hs, D, 1, D2, n->HX, 1, D, 0, n->u2, 1, D, 2LL * MX * D, 1, 0), "ix^T");
     // adjoint of inverse y -> u1p layout
@@ -1184,18 +1287,22 @@ lbm_status forward(lbm_no* n, int B, const float* in, float* out) {
         k_lift<<<grid_for(tot), 256, 0, n->stream>>>(n->a_in, n->params + n->oP, n->params + n->op, B, n->Ci, W, S, n->h0,
                                                     n->hb[0]);
     NCK(n, cudaGetLastError(), "lift");
+    int parts = 0;
     for (int l = 0; l < n->L; ++l) {
         k_f32_to_bf16<<<grid_for((long long)W * W), 256, 0, n->stream>>>(n->params + n->oWc[l], n->wcb + (long long)l * W * W,
                                                                            (long long)W * W);
-        st = l == 0 ? spectral_fwd(n, l, n->h0, 0, n->z[l]) : spectral_fwd(n, l, n->z[l - 1], 1, n->z[l]);
+        st = l == 0 ? spectral_fwd(n, l, n->h0, 0, n->z[l], 0) : spectral_fwd(n, l, n->z[l - 1], 1, n->z[l], parts);
         if (st) return st;
         // 1x1 conv accumulated onto the spectral output: z[b][o][s] += sum_c Wc[o][c] h[b][c][s]
         NCK(n, gemm(n, (int)S, W, W, B, n->hb[l], 1, S, (long long)W * S, n->wcb + (long long)l * W * W, 1, W, 0, n->z[l], 1,
                     S, (long long)W * S, 0, 1),
             "conv");
+        // the row kernel also leaves the next layer's centring sums of act(z) in cpart
+        parts = rowv && l < n->L - 1 ? n->rowparts : 0;
         if (rowv)
-            k_bias_act_v<<<grid_rows(S, (long long)B * W), 256, 0, n->stream>>>(n->z[l], n->params + n->obc[l], W, S,
-                                                                                  l < n->L - 1 ? 1 : 0, n->hb[l + 1]);
+            k_bias_act_v<<<dim3(row_blocks(S), B * W), 256, 0, n->stream>>>(n->z[l], n->params + n->obc[l], W, S,
+                                                                                  l < n->L - 1 ? 1 : 0, n->hb[l + 1],
+                                                                                  parts ? n->cpart : nullptr);
         else
             k_bias_act<<<grid_for(tot), 256, 0, n->stream>>>(n->z[l], n->params + n->obc[l], W, S, tot,
                                                             l < n->L - 1 ? 1 : 0, n->hb[l + 1]);
@@ -1225,16 +1332,38 @@ lbm_status backward(lbm_no* n, const float* dout) {
         k_project_bwd_x<<<grid_for(tot), 256, 0, n->stream>>>(dout, n->params + n->oQ, B, W, n->Co, S, n->dh);
     NCK(n, cudaGetLastError(), "project bwd");
     for (int l = L - 1; l >= 0; --l) {
-        k_act_bwd<<<grid_for(tot), 256, 0, n->stream>>>(n->dh, n->z[l], tot, l < L - 1 ? 1 : 0, n->dz, n->dzb);
-        NCK(n, reduce_bs(n, n->dz, nullptr, W, 1, n->grads + n->obc[l]), "bias db");
-        NCK(n, cudaGetLastError(), "act bwd");
-        // 1x1 weight gradient: dWc[o][c] = sum_{b,s} dz[b][o][s] h[b][c][s], split-K over s: chunks
-        // of KSPLIT as one batched GEMM per sample, the remainder as one more
+        // the row kernel leaves the row sums of dz in cpart: the bias gradient and the centring
+        // of the spectral adjoint's input
+        const int parts = n->rowparts;
+        if (parts) {
+            k_act_bwd_v<<<dim3(row_blocks(S), B * W), 256, 0, n->stream>>>(n->dh, n->z[l], S, l < L - 1 ? 1 : 0, n->dz,
+                                                                                 n->dzb, n->cpart);
+            NCK(n, cudaGetLastError(), "act bwd");
+            k_rows_to_bias<<<(W + 3) / 4, 128, 0, n->stream>>>(n->cpart, B, W, parts, n->grads + n->obc[l]);
+            NCK(n, cudaGetLastError(), "bias db");
+        } else {
+            k_act_bwd<<<grid_for(tot), 256, 0, n->stream>>>(n->dh, n->z[l], tot, l < L - 1 ? 1 : 0, n->dz, n->dzb);
+            NCK(n, reduce_bs(n, n->dz, nullptr, W, 1, n->grads + n->obc[l]), "bias db");
+            NCK(n, cudaGetLastError(), "act bwd");
+        }
+        // 1x1 weight gradient: dWc[o][c] = sum_{b,s} dz[b][o][s] h[b][c][s], split-K over s into
+        // KSPLIT-deep slices, partial [b][slice]: one launch over every sample where the
+        // copy-engine GEMM takes it, else one batched launch per sample (the remainder as one more)
         const long long kc = S < KSPLIT ? S : KSPLIT;
         const int full = (int)(S / kc);
         const long long rest = S - (long long)full * kc;
         const int nk = full + (rest > 0 ? 1 : 0);
-        for (int b = 0; b < B; ++b) {
+        bool split_done = false;
+        if (nk > 1) {
+            const cudaError_t e = gemm(n, W, W, (int)S, B, n->dzb, S, 1, (long long)W * S, n->hb[l], 1, S, (long long)W * S,
+                                       n->part, W, 1, (long long)W * W, 0, 0, nk, (int)kc);
+            if (e == cudaErrorNotSupported)
+                cudaGetLastError();
+            else
+                NCK(n, e, "conv dW");
+            split_done = e == cudaSuccess;
+        }
+        for (int b = 0; !split_done && b < B; ++b) {
             const bf16* dz_b = n->dzb + (long long)b * W * S;
             const bf16* h_b = n->hb[l] + (long long)b * W * S;
             float* part_b = n->part + (long long)b * nk * W * W;
@@ -1251,7 +1380,7 @@ lbm_status backward(lbm_no* n, const float* dout) {
         NCK(n, gemm(n, (int)S, W, W, B, n->dzb, 1, S, (long long)W * S, n->wcb + (long long)l * W * W, W, 1, 0, n->dh2, 1, S,
                     (long long)W * S, 0, 0),
             "conv dX");
-        lbm_status st = spectral_bwd(n, l, n->dz, n->dh2);
+        lbm_status st = spectral_bwd(n, l, n->dz, n->dh2, parts);
         if (st) return st;
         std::swap(n->dh, n->dh2);
     }
@@ -1367,7 +1496,8 @@ lbm_status lbm_no_create(int D, int W, int modes, int L, int Ci, int Co, int max
     alloc((void**)&n->dzb, sizeof(bf16) * act);
     alloc((void**)&n->hs, sizeof(bf16) * act);
     alloc((void**)&n->hmean, sizeof(float) * maxB * W);
-    alloc((void**)&n->cpart, sizeof(double) * maxB * W * CENTER_PARTS);
+    n->rowparts = n->S % 4 == 0 ? row_blocks(n->S) : 0;
+    alloc((void**)&n->cpart, sizeof(double) * maxB * W * std::max(CENTER_PARTS, n->rowparts));
     alloc((void**)&n->red, sizeof(float) * REDUCE_CHUNKS * std::max(std::max(W * Ci, Co * W), W));
     alloc((void**)&n->part, sizeof(float) * maxB * ((S + KSPLIT - 1) / KSPLIT + 1) * W * W);
     alloc((void**)&n->dout, sizeof(float) * maxB * Co * S);
@@ -1433,8 +1563,16 @@ lbm_status lbm_no_train_step(lbm_no* n, int batch, const float* in, const float*
     ++n->adam_t;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - powf(b1, (float)n->adam_t), c2 = 1.0f - powf(b2, (float)n->adam_t);
-    k_adam<<<grid_for(n->nparam), 256, 0, n->stream>>>(n->params, n->grads, n->adam_m, n->adam_v, n->nparam, lr, b1, b2,
-                                                        1e-8f, c1, c2);
+    // parameters in float4 groups (the four buffers are separate allocations, 16-byte aligned), the
+    // last n mod 4 one by one
+    const long long n4 = n->nparam / 4, tail = n->nparam - 4 * n4;
+    if (n4 > 0)
+        k_adam_v<<<grid_for(n4), 256, 0, n->stream>>>(reinterpret_cast<float4*>(n->params), reinterpret_cast<const float4*>(n->grads),
+                                                      reinterpret_cast<float4*>(n->adam_m), reinterpret_cast<float4*>(n->adam_v), n4,
+                                                      lr, b1, b2, 1e-8f, c1, c2);
+    if (tail > 0)
+        k_adam<<<1, 32, 0, n->stream>>>(n->params + 4 * n4, n->grads + 4 * n4, n->adam_m + 4 * n4, n->adam_v + 4 * n4, tail, lr, b1,
+                                        b2, 1e-8f, c1, c2);
     NCK(n, cudaGetLastError(), "adam");
     if (loss) NCK(n, cudaMemcpyAsync(loss, n->loss_d, sizeof(double), cudaMemcpyDeviceToHost, n->stream), "loss copy");
     return check_gemm(n);

@@ -113,7 +113,7 @@ def _operand(rng, rows, K, nb, k_major, pad):
 @pytest.mark.parametrize("a_k,b_k", [(True, True), (True, False), (False, True), (False, False)])
 @pytest.mark.parametrize("M,N,K,nb,b_shared", [(200, 40, 72, 3, False), (130, 120, 200, 2, True),
                                                 (300, 264, 136, 1, False), (64, 24, 64, 700, True),
-                                                (40, 48, 136, 301, True)])
+                                                (40, 48, 136, 301, True), (24, 40, 200, 5, False)])
 def test_gemm_tma_operand_layouts(a_k, b_k, M, N, K, nb, b_shared):
     """Operands the copy engine can address (16-byte aligned, strides multiples of 8 elements):
     each of A and B K-contiguous or M/N-contiguous, ragged M, N and K (K a multiple of 8 but not
