@@ -402,7 +402,6 @@ struct Args {
     int stage_tx;     // bytes the copies of one stage deliver (boxes no taller than the operand)
     int b_tx;         // ... of which B's (per K block, also for the resident B)
     int ksplit, kchunk_blocks;  // K slices per item and K blocks per slice
-    int l2_prefetch;            // the producer also prefetches into L2 one ring length ahead
     int b_res;        // B loaded once (every K block of the single column tile) and kept
     int stages;       // ring stages
     int stage_bytes;  // A block (+ B block unless resident)
@@ -492,16 +491,6 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
     const __nv_bfloat162 r = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&r);
-}
-
-// Prefetch of the box at (c0, c1[, c2]) into L2 (no shared-memory destination, no completion).
-__device__ __forceinline__ void tma_prefetch(const CUtensorMap* map, int c0, int c1, int c2, bool three) {
-    const uint64_t m = reinterpret_cast<uint64_t>(map);
-    if (three)
-        asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];\n" ::"l"(m), "r"(c0), "r"(c1), "r"(c2)
-                     : "memory");
-    else
-        asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];\n" ::"l"(m), "r"(c0), "r"(c1) : "memory");
 }
 
 __device__ __forceinline__ void tile_coords(const Args& g, long long t, int& b, int& m0, int& tn, int& ks) {
@@ -657,41 +646,6 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
         }
         uint32_t it = 0, s = 0, ph = 0;  // blocks issued; stage and the parity of its current use
-        // L2 prefetch cursor, one ring length ahead of the loads: the copy engine keeps few
-        // DRAM-bound requests in flight per SM, so the loads should find their data in L2
-        long long pt = blockIdx.x;
-        int pb = 0, pm0 = 0, ptn = 0, pks = 0, pkb = 0, pnkb = 0;
-        if (pt < g.tiles) {
-            tile_coords(g, pt, pb, pm0, ptn, pks);
-            pnkb = tile_kblocks(g, pks);
-        }
-        auto prefetch_next = [&]() {
-            if (pt >= g.tiles) return;
-            const int k0 = (pks * g.kchunk_blocks + pkb) * TK;
-            if (g.a_mn) {
-                tma_prefetch(&map_a, pm0, k0, pb, g.a_3d);
-                if (g.pack == 1) tma_prefetch(&map_a, pm0 + ATOM, k0, pb, g.a_3d);
-            } else {
-                tma_prefetch(&map_a, k0, pm0, pb, g.a_3d);
-            }
-            if (!g.b_res) {
-                if (g.b_mn) {
-                    for (int j = 0; j < TN / ATOM; ++j) tma_prefetch(&map_b, ptn * TN + j * ATOM, k0, pb, g.b_3d);
-                } else {
-                    tma_prefetch(&map_b, k0, ptn * TN, pb, g.b_3d);
-                }
-            }
-            if (++pkb == pnkb) {
-                pkb = 0;
-                pt += gridDim.x;
-                if (pt < g.tiles) {
-                    tile_coords(g, pt, pb, pm0, ptn, pks);
-                    pnkb = tile_kblocks(g, pks);
-                }
-            }
-        };
-        if (g.l2_prefetch)
-            for (uint32_t j = 0; j < stages; ++j) prefetch_next();
         for (long long t = blockIdx.x; t < g.tiles && !abort_flag; t += gridDim.x) {
             int b, m0, tn, ks;
             tile_coords(g, t, b, m0, tn, ks);
@@ -701,7 +655,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                     abort_flag = 1;
                     break;
                 }
-                if (g.l2_prefetch) prefetch_next();
                 const uint32_t bar = smem_u32(&full[s]);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(g.stage_tx)
                              : "memory");
@@ -1121,7 +1074,6 @@ bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* 
     a.res_bytes = a.b_res ? a.k_blocks * b_block : 0;
     a.stage_bytes = a_tx + (a.b_res ? 0 : a.b_tx);
     a.stage_tx = a.stage_bytes;
-    a.l2_prefetch = 1;
     // what the last stage's MMAs read past the end of the ring: kept inside the block's memory
     int guard = std::max(0, (a.a_mn ? a_tx : TM * TK * 2) - a.stage_bytes);
     if (!a.b_res) guard = std::max(guard, a_tx + b_block - a.stage_bytes);
