@@ -3,13 +3,15 @@
 // Each operand is addressed through one stride per dimension plus a batch stride, so transposed
 // and permuted views need no copies.  Two kernels:
 // * k_gemm_bf16_tma, for operands the tensor memory accelerator can address (16-byte aligned
-//   base, strides multiples of 8 elements, K- or M/N-contiguous): persistent blocks, one per SM,
-//   warp-specialised.  One thread streams 64-deep K blocks of A (128 rows) and B (64, 128 or 256
-//   columns) into a ring of shared-memory stages with cp.async.bulk.tensor (128-byte swizzle,
-//   rows outside the operand zero-filled), one thread issues tcgen05.mma into two tensor-memory
-//   accumulators, and two groups of four warps drain the accumulators (tcgen05.ld) and store C
+//   base, strides multiples of 8 elements, K- or M/N-contiguous): persistent, warp-specialised
+//   blocks (two per SM for 64/128-column tiles, one for 256).  One thread streams 64-deep K
+//   blocks of A (128 rows) and B (64, 128 or 256 columns) into a ring of shared-memory stages
+//   with cp.async.bulk.tensor (128-byte swizzle, rows outside the operand zero-filled), one thread
+//   issues tcgen05.mma into two tensor-memory accumulators, and one or two groups of four warps
+//   drain the accumulators (tcgen05.ld) and store C (through shared memory and the copy engine)
 //   while the next tile is loaded and multiplied.  Items of at most 64 rows against a shared B
-//   are stacked two to a 128-row tile.
+//   are stacked two to a 128-row tile; a B shared by every item stays resident; K can be split
+//   into partial products.
 // * k_gemm_bf16_tc, for every other operand: a CTA computes one 128 x TN tile of C (TN = 32, 48
 //   or 64); its 128 threads stage 64-deep K slices of A and B into shared memory in the
 //   no-swizzle K-major layout of 8 x 16-byte core matrices, in two stages, one elected thread
@@ -368,8 +370,9 @@ __global__ void __launch_bounds__(THREADS) k_gemm_bf16_tc(GemmArgs g) {
 //   warp 1 (one lane)  MMA issuer: waits for a stage, issues up to four tcgen05.mma (K = 16) into
 //                      one of two TMEM accumulators, commits the stage back to its `empty` barrier
 //                      and, after a tile's last block, the accumulator to its `tfull` barrier;
-//   warps 2-5, 6-9     epilogue, one group per accumulator: read it back (each warp its 32-lane
-//                      quarter), hand it back through `tempty`, scale and store C.
+//   warps 2-5 (6-9)    epilogue: one group for both accumulators, or one group per accumulator;
+//                      read it back (each warp its 32-lane quarter), hand it back through
+//                      `tempty`, scale and store C.
 // The producer runs ahead across tile boundaries, so the loads of the next tiles overlap the MMAs
 // and the epilogue of the current one.  A B shared by every batch item whose K blocks fit in
 // shared memory (the operator's DFT matrices and 1x1 weights) is loaded once per block and stays
@@ -379,16 +382,25 @@ __global__ void __launch_bounds__(THREADS) k_gemm_bf16_tc(GemmArgs g) {
 // zero-filled by the copy.
 namespace tma {
 
-constexpr int THREADS = 320;             // warps 0-1 roles, 2-5 and 6-9 the two epilogue groups
+// Two shapes of block: one epilogue group (192 threads, ~105 KB of shared memory, two blocks per
+// SM) for the 64- and 128-column tiles, whose products stream from DRAM: the copy engine serves
+// each block's loads with bounded concurrency, so two blocks per SM keep twice the requests in
+// flight; two groups (320 threads, ~217 KB, one block per SM) for the 256-column tile.
+template <int GROUPS>
+struct Shape {
+    static constexpr int threads = 64 + 128 * GROUPS;        // warps 0-1 roles, then the epilogue groups
+    static constexpr int blocks_per_sm = GROUPS == 1 ? 2 : 1;
+    static constexpr int smem_use = GROUPS == 1 ? 96 * 1024 : 200 * 1024;  // resident B + ring (+ C staging)
+    static constexpr int c_stage_bytes = GROUPS * 4 * 2 * 4096;            // two 4 KB boxes per epilogue warp
+};
 constexpr int ATOM = 64;                 // elements in one swizzled 128-byte row
 constexpr int MAX_STAGES = 16;
 constexpr int SMEM_ALIGN = 1024;         // the 128-byte swizzle repeats every 8 rows = 1024 B
-constexpr int SMEM_USE = 200 * 1024;     // resident B + ring (+ C staging)
-constexpr int C_STAGE_BYTES = 8 * 2 * 4096;  // two 4 KB boxes per epilogue warp
 // Unused shared memory after the ring: a descriptor whose two strides were read the other way
 // round would still address memory of this block.
 constexpr int SMEM_TAIL = 8192;
-constexpr int SMEM_BYTES = SMEM_USE + SMEM_ALIGN + SMEM_TAIL;
+template <int GROUPS>
+constexpr int smem_bytes() { return Shape<GROUPS>::smem_use + SMEM_ALIGN + SMEM_TAIL; }
 
 struct Args {
     int M, N, K, batch;
@@ -584,8 +596,8 @@ __device__ __forceinline__ void store16(const Args& g, long long off0, int n, co
     }
 }
 
-template <int TN>
-__global__ void __launch_bounds__(THREADS, 1)
+template <int TN, int GROUPS>
+__global__ void __launch_bounds__(Shape<GROUPS>::threads, Shape<GROUPS>::blocks_per_sm)
     k_gemm_bf16_tma(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                     const __grid_constant__ CUtensorMap map_c, Args g) {
     constexpr int B_BLOCK = TN * TK * 2;    // one K block of B: TN rows x 64 K
@@ -756,7 +768,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t lt = 0;
         for (long long t = blockIdx.x; t < g.tiles && !abort_flag; t += gridDim.x, ++lt) {
             const uint32_t a = lt & 1, ause = lt >> 1;
-            if ((int)a != grp) continue;
+            if (GROUPS == 2 && (int)a != grp) continue;
             int b, m0, tn, ks;
             tile_coords(g, t, b, m0, tn, ks);
             const int n0 = tn * TN;
@@ -1013,18 +1025,20 @@ int sm_count() {
     return n > 0 ? n : 1;
 }
 
-template <int TN>
+template <int TN, int GROUPS>
 cudaError_t launch_tma_tn(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mc, tma::Args a, cudaStream_t st) {
+    using Sh = tma::Shape<GROUPS>;
     static bool attr_set = false;
     if (!attr_set) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(tma::k_gemm_bf16_tma<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tma::SMEM_BYTES);
+        const cudaError_t e = cudaFuncSetAttribute(tma::k_gemm_bf16_tma<TN, GROUPS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, tma::smem_bytes<GROUPS>());
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     static const int sms = sm_count();
-    const long long grid = a.tiles < sms ? a.tiles : sms;
-    tma::k_gemm_bf16_tma<TN><<<(unsigned)grid, tma::THREADS, tma::SMEM_BYTES, st>>>(ma, mb, mc, a);
+    const long long slots = (long long)sms * Sh::blocks_per_sm;
+    const long long grid = a.tiles < slots ? a.tiles : slots;
+    tma::k_gemm_bf16_tma<TN, GROUPS><<<(unsigned)grid, Sh::threads, tma::smem_bytes<GROUPS>(), st>>>(ma, mb, mc, a);
     return cudaGetLastError();
 }
 
@@ -1070,7 +1084,11 @@ bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* 
     const int b_block = TN * TK * 2;
     // one B for every tile (shared by the batch, one column tile, no K slices) that fits in half
     // the budget
-    a.b_res = ksplit == 1 && !a.b_3d && a.tiles_n == 1 && (long long)a.k_blocks * b_block <= tma::SMEM_USE / 2;
+    // one epilogue group and two blocks per SM below 256 columns (see tma::Shape)
+    const int groups = TN == 256 ? 2 : 1;
+    const int smem_use = groups == 2 ? tma::Shape<2>::smem_use : tma::Shape<1>::smem_use;
+    const int c_stage_bytes = groups == 2 ? tma::Shape<2>::c_stage_bytes : tma::Shape<1>::c_stage_bytes;
+    a.b_res = ksplit == 1 && !a.b_3d && a.tiles_n == 1 && (long long)a.k_blocks * b_block <= smem_use / 2;
     a.res_bytes = a.b_res ? a.k_blocks * b_block : 0;
     a.stage_bytes = a_tx + (a.b_res ? 0 : a.b_tx);
     a.stage_tx = a.stage_bytes;
@@ -1086,7 +1104,7 @@ bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* 
     a.c_row = a.c_3d = 0;
     if (TN <= 128 && (!g.beta || !g.out_bf16) && c_map(&mc, g, batch * ksplit, &a.c_row, &a.c_3d))
         a.c_tma = g.beta ? 2 : 1;
-    const int ring_budget = tma::SMEM_USE - (a.c_tma ? tma::C_STAGE_BYTES : 0) - guard;
+    const int ring_budget = smem_use - (a.c_tma ? c_stage_bytes : 0) - guard;
     a.stages = (ring_budget - a.res_bytes) / a.stage_bytes;
     if (a.stages > tma::MAX_STAGES) a.stages = tma::MAX_STAGES;
     if (a.stages < 2) return false;
@@ -1101,11 +1119,11 @@ bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* 
     a.c_vec = g.c_vec;
     a.err = g.err;
     if (TN == 64)
-        *err = launch_tma_tn<64>(ma, mb, mc, a, st);
+        *err = launch_tma_tn<64, 1>(ma, mb, mc, a, st);
     else if (TN == 128)
-        *err = launch_tma_tn<128>(ma, mb, mc, a, st);
+        *err = launch_tma_tn<128, 1>(ma, mb, mc, a, st);
     else
-        *err = launch_tma_tn<256>(ma, mb, mc, a, st);
+        *err = launch_tma_tn<256, 2>(ma, mb, mc, a, st);
     return true;
 }
 
