@@ -1079,8 +1079,82 @@ __global__ void __launch_bounds__(256) k_reduce_pairs(const float* __restrict__ 
     }
 }
 
+// All pairs at once for a 32-channel operand ("big") against one of CS channels ("small"): a
+// thread streams its positions (16-byte loads, each input read once) and keeps the 32 CS pair
+// sums in registers; the warp then reduce-scatters them (after five butterfly exchanges lane l
+// holds the warp's totals of pairs 4l .. 4l + 3 for CS = 4), the warps' totals are added in FP64
+// in warp order and written as part[chunk][i Cy + j] like k_reduce_bs.  grid = chunks.
+constexpr int PAIR_CHUNKS = 256;
+
+template <int CS>
+__global__ void __launch_bounds__(256) k_reduce_pairs32(const float* __restrict__ big, const float* __restrict__ small, int B,
+                                                        long long S, int big_is_x, int Cy, float* __restrict__ part) {
+    constexpr int CB = 32, NA = CB * CS;  // accumulators per thread, index c CS + k
+    const long long S4 = S / 4, n4 = (long long)B * S4;
+    const long long per = (n4 + gridDim.x - 1) / gridDim.x;
+    const long long lo = (long long)blockIdx.x * per, hi = (lo + per < n4) ? lo + per : n4;
+    float acc[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
+    for (long long b = lo / S4; b < B && b * S4 < hi; ++b) {
+        const long long g0 = lo > b * S4 ? lo - b * S4 : 0, g1 = hi - b * S4 < S4 ? hi - b * S4 : S4;
+        const float4* bp = reinterpret_cast<const float4*>(big + b * CB * S);
+        const float4* sp = reinterpret_cast<const float4*>(small + b * CS * S);
+        for (long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+            float4 y[CS];
+#pragma unroll
+            for (int k = 0; k < CS; ++k) y[k] = __ldg(sp + k * S4 + g);
+#pragma unroll
+            for (int c = 0; c < CB; ++c) {
+                const float4 x = __ldg(bp + c * S4 + g);
+#pragma unroll
+                for (int k = 0; k < CS; ++k) {
+                    float& a = acc[c * CS + k];
+                    a = fmaf(x.x, y[k].x, a);
+                    a = fmaf(x.y, y[k].y, a);
+                    a = fmaf(x.z, y[k].z, a);
+                    a = fmaf(x.w, y[k].w, a);
+                }
+            }
+        }
+    }
+    // reduce-scatter over the warp: at offset o the lanes with bit o set keep the upper half
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16, h = NA / 2; o >= 1; o >>= 1, h >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < NA / 2; ++i)
+            if (i < h) {
+                const float send = up ? acc[i] : acc[i + h];
+                const float keep = up ? acc[i + h] : acc[i];
+                acc[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, o);
+            }
+    }
+    constexpr int PER_LANE = NA / 32;  // lane l holds accumulators PER_LANE l + i
+    __shared__ double red[8][NA];
+#pragma unroll
+    for (int i = 0; i < PER_LANE; ++i) red[warp][lane * PER_LANE + i] = acc[i];
+    __syncthreads();
+    for (int a = threadIdx.x; a < NA; a += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][a];
+        const int c = a / CS, k = a % CS;
+        const int pair = big_is_x ? c * Cy + k : k * Cy + c;
+        part[(long long)blockIdx.x * NA + pair] = (float)t;
+    }
+}
+
 cudaError_t reduce_bs(lbm_no* n, const float* X, const float* Y, int Cx, int Cy, float* out) {
     const int pairs = Cx * Cy;
+    if (Y && n->S % 4 == 0 && ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15u) == 0 &&
+        ((Cx == 32 && Cy == 4) || (Cx == 4 && Cy == 32))) {
+        const bool x_big = Cx == 32;
+        k_reduce_pairs32<4><<<PAIR_CHUNKS, 256, 0, n->stream>>>(x_big ? X : Y, x_big ? Y : X, n->B, n->S, x_big ? 1 : 0, Cy,
+                                                                 n->red);
+        k_sum_partials<<<(pairs + 31) / 32, 512, 0, n->stream>>>(n->red, PAIR_CHUNKS, pairs, out);
+        return cudaGetLastError();
+    }
     const bool al = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15u) == 0;
     if (n->S % 4 == 0 && al && (Y == nullptr || (Cx >= Cy ? Cy : Cx) <= RED_SMALL)) {
         const bool x_big = Y == nullptr || Cx >= Cy;
@@ -1498,7 +1572,7 @@ lbm_status lbm_no_create(int D, int W, int modes, int L, int Ci, int Co, int max
     alloc((void**)&n->hmean, sizeof(float) * maxB * W);
     n->rowparts = n->S % 4 == 0 ? row_blocks(n->S) : 0;
     alloc((void**)&n->cpart, sizeof(double) * maxB * W * std::max(CENTER_PARTS, n->rowparts));
-    alloc((void**)&n->red, sizeof(float) * REDUCE_CHUNKS * std::max(std::max(W * Ci, Co * W), W));
+    alloc((void**)&n->red, sizeof(float) * std::max(REDUCE_CHUNKS, PAIR_CHUNKS) * std::max(std::max(W * Ci, Co * W), W));
     alloc((void**)&n->part, sizeof(float) * maxB * ((S + KSPLIT - 1) / KSPLIT + 1) * W * W);
     alloc((void**)&n->dout, sizeof(float) * maxB * Co * S);
     alloc((void**)&n->loss_d, sizeof(double));
