@@ -445,46 +445,70 @@ __global__ void __launch_bounds__(256) k_mix_bwd_w(const float* __restrict__ dY,
         }
 }
 
-// Width-32 forms of the three mixing kernels, the operator's configuration.  One warp per mode; a
-// mode's 32 x 32 complex matrix is 8 KB contiguous ([o][c][ri]).  Each lane holds one row (forward:
-// lane = o, sixteen 16-byte loads issued together) or one column (input gradient: lane = c, 32
-// loads of 8 bytes, each a coalesced 256-byte row of the warp) of it in registers, and the mode's
-// coefficients of the other index are staged per warp in shared memory ([channel][sample][ri],
-// read back as broadcasts), four samples at a time.  Every output is summed over the channel (or
-// the sample) in the same order as the general kernels.
-constexpr int MIX_W = 32, MIX_S = 4;
+// Width-32 forms of the three mixing kernels, the operator's configuration.  One warp per mode,
+// a block of 8 warps per 8 consecutive modes: kz0 .. kz0 + 7 of one (kx, ky) (MZ a multiple of 8),
+// so the block's coefficients of one (sample, channel, ri) are one 32-byte run, loaded by the block
+// as two 16-byte vectors and scattered per mode into shared memory ([mode][channel][sample][ri]);
+// the BF16 outputs leave the same way, 16 bytes per run.  A mode's 32 x 32 complex matrix is 8 KB
+// contiguous ([o][c][ri]); each lane holds one row (forward: lane = o, sixteen 16-byte loads) or
+// one column (input gradient: lane = c, 32 loads of 8 bytes, each a coalesced 256-byte row of the
+// warp) of it in registers.  Samples go four at a time.  Every output is summed over the channel
+// (or the sample) in the same order as the general kernels.
+constexpr int MIX_W = 32, MIX_S = 4, MIX_MODES = 8;
+constexpr int MIX_BUF = MIX_W * 2 * MIX_S;  // floats per mode and sample chunk
 
-// the warp's shared buffer <- v[b0 + j][ch = lane][kx][ky][ri][kz], j < MIX_S (zeros past nb)
-__device__ __forceinline__ void stage_mode(const float* __restrict__ V, const MixDims& d, int b0, int nb, int kx, int ky,
-                                           int kz, float* sv, int lane) {
-    float t[2 * MIX_S];
-#pragma unroll
-    for (int j = 0; j < MIX_S; ++j) {
-        t[2 * j] = j < nb ? V[xidx(d, b0 + j, lane, kx, ky, 0, kz)] : 0.0f;
-        t[2 * j + 1] = j < nb ? V[xidx(d, b0 + j, lane, kx, ky, 1, kz)] : 0.0f;
+// sbuf[w][(ch MIX_S + j) 2 + ri] <- v[b0 + j][ch][kx][ky][ri][kz0 + w] (zeros for j >= nb)
+__device__ __forceinline__ void stage_block(const float* __restrict__ V, const MixDims& d, int b0, int nb, int kx, int ky,
+                                            int kz0, float (*sbuf)[MIX_BUF]) {
+    for (int r = threadIdx.x; r < MIX_S * MIX_W * 2; r += blockDim.x) {
+        const int j = r / (MIX_W * 2), ch = (r >> 1) % MIX_W, ri = r & 1;
+        float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+        if (j < nb) {
+            const float4* p = reinterpret_cast<const float4*>(V + xidx(d, b0 + j, ch, kx, ky, ri, kz0));
+            lo = __ldg(p);
+            hi = __ldg(p + 1);
+        }
+        const int off = (ch * MIX_S + j) * 2 + ri;
+        sbuf[0][off] = lo.x;
+        sbuf[1][off] = lo.y;
+        sbuf[2][off] = lo.z;
+        sbuf[3][off] = lo.w;
+        sbuf[4][off] = hi.x;
+        sbuf[5][off] = hi.y;
+        sbuf[6][off] = hi.z;
+        sbuf[7][off] = hi.w;
     }
-    float4* dst = reinterpret_cast<float4*>(sv + lane * 2 * MIX_S);
-    dst[0] = make_float4(t[0], t[1], t[2], t[3]);
-    dst[1] = make_float4(t[4], t[5], t[6], t[7]);
-    __syncwarp();
+    __syncthreads();
+}
+
+// out[b0 + j][ch][kx][ky][ri][kz0 .. + 7] <- so[(j MIX_W + ch) 2 + ri][mode], one 16-byte store per run
+__device__ __forceinline__ void unstage_block(bf16* __restrict__ out, const MixDims& d, int b0, int nb, int kx, int ky, int kz0,
+                                              const bf16 (*so)[MIX_MODES]) {
+    __syncthreads();
+    for (int r = threadIdx.x; r < nb * MIX_W * 2; r += blockDim.x) {
+        const int j = r / (MIX_W * 2), ch = (r >> 1) % MIX_W, ri = r & 1;
+        *reinterpret_cast<uint4*>(out + xidx(d, b0 + j, ch, kx, ky, ri, kz0)) = *reinterpret_cast<const uint4*>(so[r]);
+    }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(256) k_mix_fwd32(const float* __restrict__ X, const float* __restrict__ Wm, MixDims d,
                                                    bf16* __restrict__ Y) {
-    __shared__ __align__(16) float sbuf[8][MIX_W * 2 * MIX_S];
+    __shared__ __align__(16) float sbuf[MIX_MODES][MIX_BUF];
+    __shared__ __align__(16) bf16 so[MIX_S * MIX_W * 2][MIX_MODES];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long m = (long long)blockIdx.x * 8 + warp;
-    if (m >= (long long)d.MX * d.MY * d.MZ) return;
+    const long long m = (long long)blockIdx.x * MIX_MODES + warp;  // modes fill whole blocks
     int kx, ky, kz;
     mode_of(d, m, kx, ky, kz);
+    const int kz0 = kz - warp;
     const float4* w4 = reinterpret_cast<const float4*>(Wm + widx(d, kx, ky, kz, lane, 0));
     float4 w[MIX_W / 2];  // row o = lane: w[i] = (re, im) of c = 2i, 2i + 1
 #pragma unroll
     for (int i = 0; i < MIX_W / 2; ++i) w[i] = __ldg(w4 + i);
-    float* sv = sbuf[warp];
+    const float* sv = sbuf[warp];
     for (int b0 = 0; b0 < d.B; b0 += MIX_S) {
         const int nb = min(MIX_S, d.B - b0);
-        stage_mode(X, d, b0, nb, kx, ky, kz, sv, lane);
+        stage_block(X, d, b0, nb, kx, ky, kz0, sbuf);
         float yr[MIX_S], yi[MIX_S];
 #pragma unroll
         for (int j = 0; j < MIX_S; ++j) yr[j] = yi[j] = 0.0f;
@@ -500,32 +524,32 @@ __global__ void __launch_bounds__(256) k_mix_fwd32(const float* __restrict__ X, 
                 yi[j] += wr * xi[j] + wi * xr[j];
             }
         }
-        __syncwarp();
 #pragma unroll
-        for (int j = 0; j < MIX_S; ++j)
-            if (j < nb) {
-                Y[xidx(d, b0 + j, lane, kx, ky, 0, kz)] = __float2bfloat16(yr[j]);
-                Y[xidx(d, b0 + j, lane, kx, ky, 1, kz)] = __float2bfloat16(yi[j]);
-            }
+        for (int j = 0; j < MIX_S; ++j) {
+            so[(j * MIX_W + lane) * 2][warp] = __float2bfloat16(yr[j]);
+            so[(j * MIX_W + lane) * 2 + 1][warp] = __float2bfloat16(yi[j]);
+        }
+        unstage_block(Y, d, b0, nb, kx, ky, kz0, so);
     }
 }
 
 __global__ void __launch_bounds__(256) k_mix_bwd_x32(const float* __restrict__ dY, const float* __restrict__ Wm,
                                                      MixDims d, bf16* __restrict__ dX) {
-    __shared__ __align__(16) float sbuf[8][MIX_W * 2 * MIX_S];
+    __shared__ __align__(16) float sbuf[MIX_MODES][MIX_BUF];
+    __shared__ __align__(16) bf16 so[MIX_S * MIX_W * 2][MIX_MODES];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long m = (long long)blockIdx.x * 8 + warp;
-    if (m >= (long long)d.MX * d.MY * d.MZ) return;
+    const long long m = (long long)blockIdx.x * MIX_MODES + warp;
     int kx, ky, kz;
     mode_of(d, m, kx, ky, kz);
+    const int kz0 = kz - warp;
     const float2* w2 = reinterpret_cast<const float2*>(Wm + widx(d, kx, ky, kz, 0, lane));
     float2 w[MIX_W];  // column c = lane: w[o] = W[o][c]
 #pragma unroll
     for (int o = 0; o < MIX_W; ++o) w[o] = __ldg(w2 + o * MIX_W);
-    float* sv = sbuf[warp];
+    const float* sv = sbuf[warp];
     for (int b0 = 0; b0 < d.B; b0 += MIX_S) {
         const int nb = min(MIX_S, d.B - b0);
-        stage_mode(dY, d, b0, nb, kx, ky, kz, sv, lane);
+        stage_block(dY, d, b0, nb, kx, ky, kz0, sbuf);
         float xr[MIX_S], xi[MIX_S];
 #pragma unroll
         for (int j = 0; j < MIX_S; ++j) xr[j] = xi[j] = 0.0f;
@@ -541,61 +565,55 @@ __global__ void __launch_bounds__(256) k_mix_bwd_x32(const float* __restrict__ d
                 xi[j] += -wi * yr[j] + wr * yi[j];
             }
         }
-        __syncwarp();
 #pragma unroll
-        for (int j = 0; j < MIX_S; ++j)
-            if (j < nb) {
-                dX[xidx(d, b0 + j, lane, kx, ky, 0, kz)] = __float2bfloat16(xr[j]);
-                dX[xidx(d, b0 + j, lane, kx, ky, 1, kz)] = __float2bfloat16(xi[j]);
-            }
+        for (int j = 0; j < MIX_S; ++j) {
+            so[(j * MIX_W + lane) * 2][warp] = __float2bfloat16(xr[j]);
+            so[(j * MIX_W + lane) * 2 + 1][warp] = __float2bfloat16(xi[j]);
+        }
+        unstage_block(dX, d, b0, nb, kx, ky, kz0, so);
     }
 }
 
-// dW[o][c] (+)= sum_b dY[b][o] conj(X[b][c]) for B <= MIX_SB samples, lane = c: X of the lane's
-// channel in registers, every sample's dY staged; each o a coalesced 256-byte row of the warp.
+// dW[o][c] (+)= sum_b dY[b][o] conj(X[b][c]), lane = c: both staged by the block, samples four at
+// a time with the 32 (o) complex sums in registers; each o a coalesced 256-byte row of the warp.
 // `add`: accumulate onto dW, else overwrite.
-constexpr int MIX_SB = 16;
-
 __global__ void __launch_bounds__(256) k_mix_bwd_w32(const float* __restrict__ dY, const float* __restrict__ X, MixDims d,
                                                      float* __restrict__ dW, int add) {
-    __shared__ __align__(16) float sbuf[8][MIX_W * 2 * MIX_SB];
+    __shared__ __align__(16) float sy[MIX_MODES][MIX_BUF];
+    __shared__ __align__(16) float sx[MIX_MODES][MIX_BUF];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long m = (long long)blockIdx.x * 8 + warp;
-    if (m >= (long long)d.MX * d.MY * d.MZ) return;
+    const long long m = (long long)blockIdx.x * MIX_MODES + warp;
     int kx, ky, kz;
     mode_of(d, m, kx, ky, kz);
-    float xr[MIX_SB], xi[MIX_SB];
-    float* sv = sbuf[warp];
+    const int kz0 = kz - warp;
+    float gr[MIX_W], gi[MIX_W];
 #pragma unroll
-    for (int j = 0; j < MIX_SB; ++j) {
-        xr[j] = j < d.B ? X[xidx(d, j, lane, kx, ky, 0, kz)] : 0.0f;
-        xi[j] = j < d.B ? X[xidx(d, j, lane, kx, ky, 1, kz)] : 0.0f;
-    }
+    for (int o = 0; o < MIX_W; ++o) gr[o] = gi[o] = 0.0f;
+    for (int b0 = 0; b0 < d.B; b0 += MIX_S) {
+        const int nb = min(MIX_S, d.B - b0);
+        stage_block(X, d, b0, nb, kx, ky, kz0, sx);
+        stage_block(dY, d, b0, nb, kx, ky, kz0, sy);
+        const float4 x01 = *reinterpret_cast<const float4*>(&sx[warp][lane * 2 * MIX_S]);
+        const float4 x23 = *reinterpret_cast<const float4*>(&sx[warp][lane * 2 * MIX_S + 4]);
+        const float xr[MIX_S] = {x01.x, x01.z, x23.x, x23.z}, xi[MIX_S] = {x01.y, x01.w, x23.y, x23.w};
 #pragma unroll
-    for (int j = 0; j < MIX_SB; j += 2)
-        if (j < d.B) {
-            const bool two = j + 1 < d.B;
-            *reinterpret_cast<float4*>(sv + (lane * MIX_SB + j) * 2) =
-                make_float4(dY[xidx(d, j, lane, kx, ky, 0, kz)], dY[xidx(d, j, lane, kx, ky, 1, kz)],
-                            two ? dY[xidx(d, j + 1, lane, kx, ky, 0, kz)] : 0.0f, two ? dY[xidx(d, j + 1, lane, kx, ky, 1, kz)] : 0.0f);
-        }
-    __syncwarp();
-    float2* w2 = reinterpret_cast<float2*>(dW + widx(d, kx, ky, kz, 0, lane));
-#pragma unroll 4
-    for (int o = 0; o < MIX_W; ++o) {
-        float gr = 0.0f, gi = 0.0f;
+        for (int o = 0; o < MIX_W; ++o) {
+            const float4 y01 = *reinterpret_cast<const float4*>(&sy[warp][o * 2 * MIX_S]);
+            const float4 y23 = *reinterpret_cast<const float4*>(&sy[warp][o * 2 * MIX_S + 4]);
+            const float yr[MIX_S] = {y01.x, y01.z, y23.x, y23.z}, yi[MIX_S] = {y01.y, y01.w, y23.y, y23.w};
 #pragma unroll
-        for (int j = 0; j < MIX_SB; j += 2)
-            if (j < d.B) {
-                const float4 y = *reinterpret_cast<const float4*>(sv + (o * MIX_SB + j) * 2);
-                gr += y.x * xr[j] + y.y * xi[j];
-                gi += -y.x * xi[j] + y.y * xr[j];
-                if (j + 1 < d.B) {
-                    gr += y.z * xr[j + 1] + y.w * xi[j + 1];
-                    gi += -y.z * xi[j + 1] + y.w * xr[j + 1];
+            for (int j = 0; j < MIX_S; ++j)
+                if (j < nb) {
+                    gr[o] += yr[j] * xr[j] + yi[j] * xi[j];
+                    gi[o] += -yr[j] * xi[j] + yi[j] * xr[j];
                 }
-            }
-        float2 v = make_float2(gr, gi);
+        }
+        __syncthreads();  // the next chunk's staging overwrites sx, sy
+    }
+    float2* w2 = reinterpret_cast<float2*>(dW + widx(d, kx, ky, kz, 0, lane));
+#pragma unroll
+    for (int o = 0; o < MIX_W; ++o) {
+        float2 v = make_float2(gr[o], gi[o]);
         if (add) {
             const float2 p = w2[o * MIX_W];
             v.x += p.x;
@@ -604,6 +622,7 @@ __global__ void __launch_bounds__(256) k_mix_bwd_w32(const float* __restrict__ d
         w2[o * MIX_W] = v;
     }
 }
+
 
 // One chunk of the B * S positions per block, one (i, j) pair per group of blocks:
 // part[chunk][i * Cy + j] = sum over the chunk of X[b][i][s] * Y[b][j][s] (X alone if Y is null).
@@ -1240,7 +1259,7 @@ lbm_status upload_dft(lbm_no* n) {
 
 // the width-32 mixing kernels apply: W = 32 and the mode matrices 16-byte aligned
 bool mix32(const lbm_no* n, const float* wm) {
-    return n->W == MIX_W && n->B <= MIX_SB && (reinterpret_cast<uintptr_t>(wm) & 15u) == 0;
+    return n->W == MIX_W && n->MZ % MIX_MODES == 0 && (reinterpret_cast<uintptr_t>(wm) & 15u) == 0;
 }
 
 // spectral convolution of layer l: input h = act(src) (FP32 [B][W][S], act = GELU if use_gelu) ->
