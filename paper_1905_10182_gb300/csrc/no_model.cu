@@ -450,10 +450,10 @@ __global__ void __launch_bounds__(256) k_mix_bwd_w(const float* __restrict__ dY,
 // so the block's coefficients of one (sample, channel, ri) are one 32-byte run, loaded by the block
 // as two 16-byte vectors and scattered per mode into shared memory ([mode][channel][sample][ri]);
 // the BF16 outputs leave the same way, 16 bytes per run.  A mode's 32 x 32 complex matrix is 8 KB
-// contiguous ([o][c][ri]); each lane holds one row (forward: lane = o, sixteen 16-byte loads) or
-// one column (input gradient: lane = c, 32 loads of 8 bytes, each a coalesced 256-byte row of the
-// warp) of it in registers.  Samples go four at a time.  Every output is summed over the channel
-// (or the sample) in the same order as the general kernels.
+// contiguous ([o][c][ri]); its warp copies it into padded shared-memory rows with cp.async
+// (coalesced) while the block stages the coefficients, then each lane reads one row (forward:
+// lane = o) or one column (input gradient: lane = c) of it.  Samples go four at a time.  Every
+// output is summed over the channel (or the sample) in the same order as the general kernels.
 constexpr int MIX_W = 32, MIX_S = 4, MIX_MODES = 8;
 constexpr int MIX_BUF = MIX_W * 2 * MIX_S;  // floats per mode and sample chunk
 
@@ -492,8 +492,33 @@ __device__ __forceinline__ void unstage_block(bf16* __restrict__ out, const MixD
     __syncthreads();
 }
 
+// A mode's 32 x 32 complex matrix (8 KB, rows o of 64 floats) into shared memory rows padded to
+// MIX_PITCH floats, by the warp with cp.async (16 bytes per lane and copy, coalesced 512-byte
+// reads): lanes reading one 16-byte chunk of 8 different rows, or 32 consecutive 8-byte words of
+// one row, then meet no bank conflict.
+constexpr int MIX_PITCH = 2 * MIX_W + 4;
+constexpr int MIX_SMAT = MIX_MODES * MIX_W * MIX_PITCH * (int)sizeof(float);  // 69,632 B of dynamic shared memory
+
+__device__ __forceinline__ void load_mode_matrix(float* sw, const float* __restrict__ w, int lane) {
+    const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(sw));
+#pragma unroll
+    for (int i = 0; i < MIX_W / 2; ++i) {
+        const int q = i * 32 + lane, o = q >> 4, c4 = q & 15;  // 16-byte chunk c4 of row o
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + (uint32_t)((o * MIX_PITCH + c4 * 4) * 4)),
+                     "l"(w + q * 4)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void wait_mode_matrix() {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(256) k_mix_fwd32(const float* __restrict__ X, const float* __restrict__ Wm, MixDims d,
                                                    bf16* __restrict__ Y) {
+    extern __shared__ __align__(16) float smat[];  // MIX_MODES matrices, MIX_W rows of MIX_PITCH
     __shared__ __align__(16) float sbuf[MIX_MODES][MIX_BUF];
     __shared__ __align__(16) bf16 so[MIX_S * MIX_W * 2][MIX_MODES];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -501,20 +526,22 @@ __global__ void __launch_bounds__(256) k_mix_fwd32(const float* __restrict__ X, 
     int kx, ky, kz;
     mode_of(d, m, kx, ky, kz);
     const int kz0 = kz - warp;
-    const float4* w4 = reinterpret_cast<const float4*>(Wm + widx(d, kx, ky, kz, lane, 0));
-    float4 w[MIX_W / 2];  // row o = lane: w[i] = (re, im) of c = 2i, 2i + 1
-#pragma unroll
-    for (int i = 0; i < MIX_W / 2; ++i) w[i] = __ldg(w4 + i);
+    float* sw = smat + warp * MIX_W * MIX_PITCH;
+    load_mode_matrix(sw, Wm + widx(d, kx, ky, kz, 0, 0), lane);
+    const float* wrow = sw + lane * MIX_PITCH;  // row o = lane
     const float* sv = sbuf[warp];
     for (int b0 = 0; b0 < d.B; b0 += MIX_S) {
         const int nb = min(MIX_S, d.B - b0);
         stage_block(X, d, b0, nb, kx, ky, kz0, sbuf);
+        if (b0 == 0) wait_mode_matrix();
         float yr[MIX_S], yi[MIX_S];
 #pragma unroll
         for (int j = 0; j < MIX_S; ++j) yr[j] = yi[j] = 0.0f;
 #pragma unroll
         for (int c = 0; c < MIX_W; ++c) {
-            const float wr = (c & 1) ? w[c >> 1].z : w[c >> 1].x, wi = (c & 1) ? w[c >> 1].w : w[c >> 1].y;
+            // two channels per 16-byte read (conflict-free across 8 lanes with the padded rows)
+            const float4 wq = *reinterpret_cast<const float4*>(wrow + 4 * (c >> 1));
+            const float wr = (c & 1) ? wq.z : wq.x, wi = (c & 1) ? wq.w : wq.y;
             const float4 x01 = *reinterpret_cast<const float4*>(sv + c * 2 * MIX_S);
             const float4 x23 = *reinterpret_cast<const float4*>(sv + c * 2 * MIX_S + 4);
             const float xr[MIX_S] = {x01.x, x01.z, x23.x, x23.z}, xi[MIX_S] = {x01.y, x01.w, x23.y, x23.w};
@@ -535,6 +562,7 @@ __global__ void __launch_bounds__(256) k_mix_fwd32(const float* __restrict__ X, 
 
 __global__ void __launch_bounds__(256) k_mix_bwd_x32(const float* __restrict__ dY, const float* __restrict__ Wm,
                                                      MixDims d, bf16* __restrict__ dX) {
+    extern __shared__ __align__(16) float smat[];  // MIX_MODES matrices, MIX_W rows of MIX_PITCH
     __shared__ __align__(16) float sbuf[MIX_MODES][MIX_BUF];
     __shared__ __align__(16) bf16 so[MIX_S * MIX_W * 2][MIX_MODES];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -542,20 +570,21 @@ __global__ void __launch_bounds__(256) k_mix_bwd_x32(const float* __restrict__ d
     int kx, ky, kz;
     mode_of(d, m, kx, ky, kz);
     const int kz0 = kz - warp;
-    const float2* w2 = reinterpret_cast<const float2*>(Wm + widx(d, kx, ky, kz, 0, lane));
-    float2 w[MIX_W];  // column c = lane: w[o] = W[o][c]
-#pragma unroll
-    for (int o = 0; o < MIX_W; ++o) w[o] = __ldg(w2 + o * MIX_W);
+    float* sw = smat + warp * MIX_W * MIX_PITCH;
+    load_mode_matrix(sw, Wm + widx(d, kx, ky, kz, 0, 0), lane);
+    const float* wcol = sw + 2 * lane;  // column c = lane: W[o][c] at wcol[o MIX_PITCH]
     const float* sv = sbuf[warp];
     for (int b0 = 0; b0 < d.B; b0 += MIX_S) {
         const int nb = min(MIX_S, d.B - b0);
         stage_block(dY, d, b0, nb, kx, ky, kz0, sbuf);
+        if (b0 == 0) wait_mode_matrix();
         float xr[MIX_S], xi[MIX_S];
 #pragma unroll
         for (int j = 0; j < MIX_S; ++j) xr[j] = xi[j] = 0.0f;
 #pragma unroll
         for (int o = 0; o < MIX_W; ++o) {
-            const float wr = w[o].x, wi = w[o].y;
+            const float2 wo = *reinterpret_cast<const float2*>(wcol + o * MIX_PITCH);
+            const float wr = wo.x, wi = wo.y;
             const float4 y01 = *reinterpret_cast<const float4*>(sv + o * 2 * MIX_S);
             const float4 y23 = *reinterpret_cast<const float4*>(sv + o * 2 * MIX_S + 4);
             const float yr[MIX_S] = {y01.x, y01.z, y23.x, y23.z}, yi[MIX_S] = {y01.y, y01.w, y23.y, y23.w};
@@ -1257,9 +1286,20 @@ lbm_status upload_dft(lbm_no* n) {
     return LBM_OK;
 }
 
+// the width-32 mixing kernels take MIX_SMAT bytes of dynamic shared memory (beyond the default 48 KB)
+cudaError_t mix32_attrs() {
+    static const cudaError_t e = [] {
+        cudaError_t r = cudaFuncSetAttribute(k_mix_fwd32, cudaFuncAttributeMaxDynamicSharedMemorySize, MIX_SMAT);
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(k_mix_bwd_x32, cudaFuncAttributeMaxDynamicSharedMemorySize, MIX_SMAT);
+        return r;
+    }();
+    return e;
+}
+
 // the width-32 mixing kernels apply: W = 32 and the mode matrices 16-byte aligned
 bool mix32(const lbm_no* n, const float* wm) {
-    return n->W == MIX_W && n->MZ % MIX_MODES == 0 && (reinterpret_cast<uintptr_t>(wm) & 15u) == 0;
+    return n->W == MIX_W && n->MZ % MIX_MODES == 0 && (reinterpret_cast<uintptr_t>(wm) & 15u) == 0 &&
+           mix32_attrs() == cudaSuccess;
 }
 
 // spectral convolution of layer l: input h = act(src) (FP32 [B][W][S], act = GELU if use_gelu) ->
@@ -1289,7 +1329,7 @@ lbm_status spectral_fwd(lbm_no* n, int l, const float* src, int use_gelu, float*
     MixDims md{B, W, MX, MY, MZ};
     const unsigned mix_grid = (unsigned)(((long long)MX * MY * MZ + 7) / 8);
     if (mix32(n, n->params + n->oWm[l]))
-        k_mix_fwd32<<<mix_grid, 256, 0, n->stream>>>(n->Xh[l], n->params + n->oWm[l], md, n->yh);
+        k_mix_fwd32<<<mix_grid, 256, MIX_SMAT, n->stream>>>(n->Xh[l], n->params + n->oWm[l], md, n->yh);
     else
         k_mix_fwd<<<mix_grid, 256, 0, n->stream>>>(n->Xh[l], n->params + n->oWm[l], md, n->yh);
     NCK(n, cudaGetLastError(), "mix");
@@ -1337,7 +1377,7 @@ lbm_status spectral_bwd(lbm_no* n, int l, const float* dz, float* dh, int parts)
         // the gradient buffer was zeroed by backward() and this is the only writer of the block
         k_mix_bwd_w32<<<mix_grid, 256, 0, n->stream>>>(n->dyh, n->Xh[l], md, n->grads + n->oWm[l], 0);
         NCK(n, cudaGetLastError(), "mix dW");
-        k_mix_bwd_x32<<<mix_grid, 256, 0, n->stream>>>(n->dyh, n->params + n->oWm[l], md, n->yh);
+        k_mix_bwd_x32<<<mix_grid, 256, MIX_SMAT, n->stream>>>(n->dyh, n->params + n->oWm[l], md, n->yh);
     } else {
         k_mix_bwd_w<<<mix_grid, 256, 0, n->stream>>>(n->dyh, n->Xh[l], md, n->grads + n->oWm[l]);
         NCK(n, cudaGetLastError(), "mix dW");
