@@ -375,8 +375,15 @@ LBM_API lbm_status lbm_no_forward(lbm_no* n, int batch, const float* in, float* 
 /* Gradient of sum(dout * out) of the last forward with respect to every parameter. */
 LBM_API lbm_status lbm_no_backward(lbm_no* n, const float* dout);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error over all outputs;
- * loss (optional, host) receives the loss before the step.  in, target: device pointers. */
+ * loss (optional, host) receives the loss before the step.  in, target: device or host pointers,
+ * copied into the operator's buffers on its stream. */
 LBM_API lbm_status lbm_no_train_step(lbm_no* n, int batch, const float* in, const float* target, float lr, double* loss);
+/* enable != 0 (the default): from the second lbm_no_train_step on, the step (forward, loss,
+ * backward, Adam) is captured once per batch size as a CUDA graph on a private stream and replayed,
+ * ordered after the operator's stream by events; the inputs are first copied into the operator's
+ * buffers.  The replayed kernels are the eager ones in the same order, so results are identical.
+ * If a capture fails the operator trains eagerly from then on.  enable = 0: always eager. */
+LBM_API lbm_status lbm_no_use_graphs(lbm_no* n, int enable);
 /* A call that returns LBM_ERR_TIMEOUT (a tensor-core wait gave up) leaves the operator's outputs,
  * gradients, parameters and Adam state undefined: destroy it and create a new one. */
 LBM_API const char* lbm_no_last_error(const lbm_no* n);

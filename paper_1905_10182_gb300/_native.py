@@ -167,6 +167,8 @@ def lib():
         L.lbm_no_backward.restype = st
         L.lbm_no_train_step.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
         L.lbm_no_train_step.restype = st
+        L.lbm_no_use_graphs.argtypes = [_P, ctypes.c_int]
+        L.lbm_no_use_graphs.restype = st
         L.lbm_no_last_error.argtypes = [_P]
         L.lbm_no_last_error.restype = ctypes.c_char_p
         L.lbm_no_destroy.argtypes = [_P]

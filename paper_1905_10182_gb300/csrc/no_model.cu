@@ -734,8 +734,9 @@ __device__ __forceinline__ void adam1(float& p, float g, float& m, float& v, flo
 
 // The same update four parameters per access (n4 = n / 4 float4 groups; the tail goes to k_adam).
 __global__ void __launch_bounds__(256) k_adam_v(float4* __restrict__ p, const float4* __restrict__ g, float4* __restrict__ m,
-                                                float4* __restrict__ v, long long n4, float lr, float b1, float b2, float eps,
-                                                float c1, float c2) {
+                                                float4* __restrict__ v, long long n4, const float* __restrict__ sc, float b1,
+                                                float b2, float eps) {
+    const float lr = sc[0], c1 = sc[1], c2 = sc[2];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
         const float4 gi = g[i];
         float4 pi = p[i], mi = m[i], vi = v[i];
@@ -749,8 +750,15 @@ __global__ void __launch_bounds__(256) k_adam_v(float4* __restrict__ p, const fl
     }
 }
 
+__global__ void k_set_adam_scalars(float* __restrict__ sc, float lr, float c1, float c2) {
+    sc[0] = lr;
+    sc[1] = c1;
+    sc[2] = c2;
+}
+
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v, long long n,
-                       float lr, float b1, float b2, float eps, float c1, float c2) {
+                       const float* __restrict__ sc, float b1, float b2, float eps) {
+    const float lr = sc[0], c1 = sc[1], c2 = sc[2];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.0f - b1) * gi;
@@ -959,6 +967,16 @@ struct lbm_no {
     float* dout = nullptr;
     double* loss_d = nullptr;
     unsigned int* gemm_err = nullptr;
+    // training step as a CUDA graph: captured on a private stream for one batch size and replayed,
+    // ordered after the caller's stream by events; it reads only the operator's own buffers
+    float* tgt = nullptr;      // copy of the target [maxB][Co][S]
+    float* adam_sc = nullptr;  // Adam's step-dependent scalars on the device: lr, 1 - b1^t, 1 - b2^t
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t step_graph = nullptr;
+    int graph_B = 0;          // batch the graph holds (0: none)
+    bool graph_off = false;   // capture failed: train eagerly from then on
+    long long eager_steps = 0;
 };
 
 namespace {
@@ -1405,12 +1423,13 @@ lbm_status ensure_batch(lbm_no* n, int B) {
     return LBM_OK;
 }
 
+// in == nullptr: the input is already in a_in
 lbm_status forward(lbm_no* n, int B, const float* in, float* out) {
     lbm_status st = ensure_batch(n, B);
     if (st) return st;
     const int W = n->W;
     const long long S = n->S, tot = (long long)B * W * S;
-    NCK(n, cudaMemcpyAsync(n->a_in, in, sizeof(float) * B * n->Ci * S, cudaMemcpyDefault, n->stream), "input copy");
+    if (in) NCK(n, cudaMemcpyAsync(n->a_in, in, sizeof(float) * B * n->Ci * S, cudaMemcpyDefault, n->stream), "input copy");
     // the row-vectorised maps need S a multiple of 4; every buffer here is 16-byte aligned
     const bool rowv = S % 4 == 0;
     if (rowv && n->Ci <= VEC_CH)
@@ -1635,6 +1654,8 @@ lbm_status lbm_no_create(int D, int W, int modes, int L, int Ci, int Co, int max
     alloc((void**)&n->part, sizeof(float) * maxB * ((S + KSPLIT - 1) / KSPLIT + 1) * W * W);
     alloc((void**)&n->dout, sizeof(float) * maxB * Co * S);
     alloc((void**)&n->loss_d, sizeof(double));
+    alloc((void**)&n->tgt, sizeof(float) * maxB * Co * S);
+    alloc((void**)&n->adam_sc, sizeof(float) * 4);
     alloc((void**)&n->gemm_err, sizeof(unsigned int));
     if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA);
     if (upload_dft(n) != LBM_OK) return bail(LBM_ERR_CUDA);
@@ -1682,33 +1703,110 @@ lbm_status lbm_no_backward(lbm_no* n, const float* dout) {
     return check_gemm(n);
 }
 
-lbm_status lbm_no_train_step(lbm_no* n, int batch, const float* in, const float* target, float lr, double* loss) {
-    if (!n || !in || !target) return LBM_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// forward from a_in, MSE against tgt, backward, Adam with the scalars in adam_sc: everything the
+// training-step graph holds
+lbm_status step_body(lbm_no* n, int batch) {
     float* out = n->dout;  // the prediction is written here, then overwritten by its gradient
-    lbm_status st = forward(n, batch, in, out);
+    lbm_status st = forward(n, batch, nullptr, out);
     if (st) return st;
     const long long cnt = (long long)batch * n->Co * n->S;
     NCK(n, cudaMemsetAsync(n->loss_d, 0, sizeof(double), n->stream), "loss reset");
-    k_mse<<<grid_for(cnt), 256, 0, n->stream>>>(out, target, cnt, n->dout, n->loss_d);
+    k_mse<<<grid_for(cnt), 256, 0, n->stream>>>(out, n->tgt, cnt, n->dout, n->loss_d);
     NCK(n, cudaGetLastError(), "loss");
     st = backward(n, n->dout);
     if (st) return st;
-    ++n->adam_t;
     const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.0f - powf(b1, (float)n->adam_t), c2 = 1.0f - powf(b2, (float)n->adam_t);
     // parameters in float4 groups (the four buffers are separate allocations, 16-byte aligned), the
     // last n mod 4 one by one
     const long long n4 = n->nparam / 4, tail = n->nparam - 4 * n4;
     if (n4 > 0)
         k_adam_v<<<grid_for(n4), 256, 0, n->stream>>>(reinterpret_cast<float4*>(n->params), reinterpret_cast<const float4*>(n->grads),
                                                       reinterpret_cast<float4*>(n->adam_m), reinterpret_cast<float4*>(n->adam_v), n4,
-                                                      lr, b1, b2, 1e-8f, c1, c2);
+                                                      n->adam_sc, b1, b2, 1e-8f);
     if (tail > 0)
-        k_adam<<<1, 32, 0, n->stream>>>(n->params + 4 * n4, n->grads + 4 * n4, n->adam_m + 4 * n4, n->adam_v + 4 * n4, tail, lr, b1,
-                                        b2, 1e-8f, c1, c2);
+        k_adam<<<1, 32, 0, n->stream>>>(n->params + 4 * n4, n->grads + 4 * n4, n->adam_m + 4 * n4, n->adam_v + 4 * n4, tail, n->adam_sc,
+                                        b1, b2, 1e-8f);
     NCK(n, cudaGetLastError(), "adam");
+    return LBM_OK;
+}
+
+// Capture step_body for `batch` on the private stream; false (and graphs off) if anything fails.
+bool capture_step(lbm_no* n, int batch) {
+    if (n->step_graph) {
+        cudaGraphExecDestroy(n->step_graph);
+        n->step_graph = nullptr;
+        n->graph_B = 0;
+    }
+    if (!n->gstream && cudaStreamCreateWithFlags(&n->gstream, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (!n->ev_in && cudaEventCreateWithFlags(&n->ev_in, cudaEventDisableTiming) != cudaSuccess) return false;
+    if (!n->ev_out && cudaEventCreateWithFlags(&n->ev_out, cudaEventDisableTiming) != cudaSuccess) return false;
+    cudaStream_t user = n->stream;
+    if (cudaStreamBeginCapture(n->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    n->stream = n->gstream;
+    const lbm_status st = step_body(n, batch);
+    n->stream = user;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(n->gstream, &g);
+    bool ok = st == LBM_OK && e == cudaSuccess && g;
+    if (ok) ok = cudaGraphInstantiate(&n->step_graph, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        n->step_graph = nullptr;
+        cudaGetLastError();
+        n->err.clear();
+        return false;
+    }
+    n->graph_B = batch;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_no_train_step(lbm_no* n, int batch, const float* in, const float* target, float lr, double* loss) {
+    if (!n || !in || !target) return LBM_ERR_ARG;
+    lbm_status st = ensure_batch(n, batch);
+    if (st) return st;
+    const long long S = n->S;
+    // the step reads only the operator's buffers: input, target and Adam's scalars go there first
+    NCK(n, cudaMemcpyAsync(n->a_in, in, sizeof(float) * batch * n->Ci * S, cudaMemcpyDefault, n->stream), "input copy");
+    NCK(n, cudaMemcpyAsync(n->tgt, target, sizeof(float) * batch * n->Co * S, cudaMemcpyDefault, n->stream), "target copy");
+    ++n->adam_t;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)n->adam_t), c2 = 1.0f - powf(b2, (float)n->adam_t);
+    k_set_adam_scalars<<<1, 1, 0, n->stream>>>(n->adam_sc, lr, c1, c2);
+    NCK(n, cudaGetLastError(), "adam scalars");
+    // the first step runs eagerly (one-time set-up of kernel attributes), later ones replay a graph
+    bool replayed = false;
+    if (!n->graph_off && n->eager_steps > 0) {
+        if (n->graph_B != batch && !capture_step(n, batch)) n->graph_off = true;
+        if (n->step_graph && n->graph_B == batch) {
+            NCK(n, cudaEventRecord(n->ev_in, n->stream), "event");
+            NCK(n, cudaStreamWaitEvent(n->gstream, n->ev_in, 0), "event wait");
+            NCK(n, cudaGraphLaunch(n->step_graph, n->gstream), "graph launch");
+            NCK(n, cudaEventRecord(n->ev_out, n->gstream), "event");
+            NCK(n, cudaStreamWaitEvent(n->stream, n->ev_out, 0), "event wait");
+            replayed = true;
+        }
+    }
+    if (!replayed) {
+        st = step_body(n, batch);
+        if (st) return st;
+        ++n->eager_steps;
+    }
     if (loss) NCK(n, cudaMemcpyAsync(loss, n->loss_d, sizeof(double), cudaMemcpyDeviceToHost, n->stream), "loss copy");
     return check_gemm(n);
+}
+
+lbm_status lbm_no_use_graphs(lbm_no* n, int enable) {
+    if (!n) return LBM_ERR_ARG;
+    n->graph_off = !enable;
+    return LBM_OK;
 }
 
 const char* lbm_no_last_error(const lbm_no* n) { return n ? n->err.c_str() : ""; }
@@ -1720,6 +1818,15 @@ void lbm_no_destroy(lbm_no* n) {
                     n->HX, n->t1, n->t2, n->t2p, n->yh, n->dyh, n->u1, n->u1p, n->u2, n->dh, n->dh2, n->dz, n->dzb, n->hs, n->hmean, n->cpart, n->red,
                     n->part, n->dout, n->loss_d, n->gemm_err};
     for (void* b : bufs) cudaFree(b);
+    cudaFree(n->tgt);
+    cudaFree(n->adam_sc);
+    if (n->step_graph) cudaGraphExecDestroy(n->step_graph);
+    if (n->ev_in) cudaEventDestroy(n->ev_in);
+    if (n->ev_out) cudaEventDestroy(n->ev_out);
+    if (n->gstream) {
+        cudaStreamSynchronize(n->gstream);
+        cudaStreamDestroy(n->gstream);
+    }
     for (bf16* b : n->hb) cudaFree(b);
     for (float* b : n->z) cudaFree(b);
     for (float* b : n->Xh) cudaFree(b);

@@ -64,6 +64,10 @@ class NeuralOperator:
     def backward(self, dout):
         self._check(self._lib.lbm_no_backward(self._h, nat.ptr(dout)))
 
+    def use_graphs(self, enable=True):
+        """Replay the training step as a CUDA graph (default) or run it eagerly."""
+        self._check(self._lib.lbm_no_use_graphs(self._h, 1 if enable else 0))
+
     def train_step(self, inp, target, lr):
         loss = ctypes.c_double()
         self._check(self._lib.lbm_no_train_step(self._h, int(inp.shape[0]), nat.ptr(inp), nat.ptr(target),
