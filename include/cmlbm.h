@@ -342,9 +342,14 @@ LBM_API void lbm_batch_destroy(lbm_batch* b);
  * operator runs on:  C[b] = alpha * A[b] x B[b]  (beta != 0: C[b] += ...),  b < batch.
  * Element (m, k) of A[b] is at A + b*sab + m*sam + k*sak (BF16 elements), (k, n) of B at
  * B + b*sbb + k*sbk + n*sbn, (m, n) of C at C + b*scb + m*scm + n*scn (FP32, or BF16 with
- * out_bf16).  All pointers are device memory; err is a device flag set to 1 if an internal
- * bounded wait timed out, after which C is undefined (MMAs committed before the timeout may still
- * be writing it).  Enqueued on stream; LBM_ERR_ARG on bad sizes. */
+ * out_bf16).  All pointers are device memory.  When A and B are 16-byte aligned with one unit
+ * stride and the other strides multiples of 8 elements (K- or M/N-contiguous), the operands are
+ * streamed by the tensor memory accelerator (persistent warp-specialised kernel; C written through
+ * shared memory by the copy engine where C is row- or column-contiguous and aligned); any other
+ * layout goes through a register-staged kernel.  Both give the same products up to FP32
+ * summation order.  err is a device flag set to 1 if an internal bounded wait timed out, after
+ * which C is undefined (MMAs committed before the timeout may still be writing it).  Enqueued on
+ * stream; LBM_ERR_ARG on bad sizes. */
 LBM_API lbm_status lbm_gemm_bf16(int M, int N, int K, int batch, const void* A, long long sam, long long sak,
                                  long long sab, const void* B, long long sbk, long long sbn, long long sbb, void* C,
                                  long long scm, long long scn, long long scb, int out_bf16, float alpha, int beta,
