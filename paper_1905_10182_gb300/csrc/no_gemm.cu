@@ -1129,8 +1129,33 @@ bool try_launch_tma(const GemmArgs& g, int batch, cudaStream_t st, cudaError_t* 
 
 }  // namespace
 
+namespace {
+
+// K = 0: the product is an empty sum, so C = 0 without beta (and C is left as it is with beta).
+__global__ void k_gemm_zero_c(GemmArgs g, int batch) {
+    const long long total = (long long)batch * g.M * g.N;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / ((long long)g.M * g.N), r = i - b * g.M * g.N;
+        const long long m = r / g.N, n = r - m * g.N;
+        const long long off = b * g.scb + m * g.scm + n * g.scn;
+        if (g.out_bf16)
+            reinterpret_cast<__nv_bfloat16*>(g.C)[off] = __float2bfloat16(0.0f);
+        else
+            reinterpret_cast<float*>(g.C)[off] = 0.0f;
+    }
+}
+
+}  // namespace
+
 cudaError_t launch_gemm_bf16(const GemmArgs& g_in, int batch, cudaStream_t st) {
     if (g_in.M <= 0 || g_in.N <= 0 || g_in.K < 0 || batch <= 0) return cudaErrorInvalidValue;
+    if (g_in.K == 0) {
+        if (g_in.beta) return cudaSuccess;
+        const long long total = (long long)batch * g_in.M * g_in.N;
+        const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+        k_gemm_zero_c<<<(unsigned)blocks, 256, 0, st>>>(g_in, batch);
+        return cudaGetLastError();
+    }
     GemmArgs g = g_in;
     // C stored as 16-byte vectors: 1 FP32 (4 per vector), 2 BF16 (8 per vector), 0 element by element
     const int per = g.out_bf16 ? 8 : 4;

@@ -162,3 +162,24 @@ def test_gemm_tma_alpha_beta_epilogue(out_bf16, c_row_major, beta):
     if out_bf16:
         bound = bound + 2.0 ** -8 * np.abs(ref)
     _check(C.float().cpu().numpy(), ref, bound)
+
+
+@pytest.mark.parametrize("beta", [0, 1])
+def test_gemm_empty_k_and_thin_shapes(beta):
+    """K = 0 is an empty sum: C = 0, or C unchanged with beta.  Then products with one row, one
+    column or K = 1 against their FP64 values."""
+    M, N = 37, 29
+    C0 = torch.randn(M, N, generator=torch.Generator().manual_seed(4))
+    C = C0.clone().cuda()
+    A = torch.zeros(M, 1, dtype=torch.bfloat16, device="cuda")
+    B = torch.zeros(1, N, dtype=torch.bfloat16, device="cuda")
+    _gemm(M, N, 0, 1, A, (1, 1, 0), B, (N, 1, 0), C, (N, 1, 0), beta=beta)
+    assert torch.equal(C.cpu(), C0 if beta else torch.zeros(M, N))
+    g = torch.Generator().manual_seed(6)
+    for (M, N, K) in [(1, 40, 72), (40, 1, 72), (56, 48, 1), (1, 1, 8)]:
+        A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+        B = torch.randn(K, N, generator=g).to(torch.bfloat16)
+        C = torch.empty(M, N, device="cuda")
+        _gemm(M, N, K, 1, A.cuda(), (K, 1, 0), B.cuda(), (N, 1, 0), C, (N, 1, 0))
+        a, b = A.float().numpy().astype(np.float64), B.float().numpy().astype(np.float64)
+        _check(C.cpu().numpy(), a @ b, 2.0 ** -20 * (np.abs(a) @ np.abs(b)))
