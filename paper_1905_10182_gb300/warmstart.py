@@ -126,18 +126,22 @@ def predict(net, metas, density=True):
     (rho, ux, uy, uz) and the inference wall time."""
     import torch
     n = metas[0]["nx"]
-    out = torch.empty((1, 4, n, n, n), device="cuda")
+    nb = max(1, int(getattr(net, "max_batch", 1)))  # domains per forward
+    out = torch.empty((nb, 4, n, n, n), device="cuda")
     init = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for c in metas:
-        net.forward(torch.from_numpy(features(c)[None]).cuda(), out)
-        p = out[0].cpu().numpy().astype(np.float64)
-        ur = u_ref(c)
-        fluid = c["mask"] == 0
-        u = [np.where(fluid, p[k] * ur, 0.0).astype(np.float32) for k in range(3)]
-        rho = np.where(fluid, 1.0 + p[3] * ur, 1.0).astype(np.float32) if density else np.ones_like(u[0])
-        init.append((rho, u[0], u[1], u[2]))
+    for j in range(0, len(metas), nb):
+        group = metas[j:j + nb]
+        x = torch.from_numpy(np.stack([features(c) for c in group])).cuda()
+        net.forward(x, out[:len(group)])
+        preds = out[:len(group)].cpu().numpy().astype(np.float64)
+        for c, p in zip(group, preds):
+            ur = u_ref(c)
+            fluid = c["mask"] == 0
+            u = [np.where(fluid, p[k] * ur, 0.0).astype(np.float32) for k in range(3)]
+            rho = np.where(fluid, 1.0 + p[3] * ur, 1.0).astype(np.float32) if density else np.ones_like(u[0])
+            init.append((rho, u[0], u[1], u[2]))
     torch.cuda.synchronize()
     return init, time.perf_counter() - t0
 
